@@ -1,0 +1,356 @@
+"""Benchmark: GB/s of 100-byte records sorted on one GB300.
+
+Default workload: the 10 GB internal sort -- 100,000,000 records x 100 B,
+uniform 10-byte keys and 90-byte values from a seed, resident in HBM
+(inputs and outputs are 10 GB each, far larger than the 129 MB L2, so no L2
+flush is needed between steps).  One step = one ley_sort_records call:
+key extraction, MSD radix passes, small-bucket finishing and the record
+gather.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``value`` is device-timed (CUDA events on the sorting
+stream); ``e2e`` is the same metric through the C ABI with pinned host
+buffers (host->device and device->host copies inside the timed region);
+``roofline`` is the dominant kernel's algorithmic bytes over its measured
+launch time against the measured HBM copy bandwidth; ``cpu_baseline`` is the
+CPU oracle timed on a bounded sample on this host.  With N > 1 (torchrun)
+every rank sorts its own replica of the workload ("replicas only": the sort
+has no exchange step) and rank 0 reports the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s of 100-byte records sorted on 1 GB300 (10 GB in-HBM)"
+REC, KEY = 100, 10
+
+# Algorithmic HBM bytes per record for each kernel of the internal sort of
+# uniform 10-byte keys (reads + writes): the bytes the method must move.
+ALG_BYTES = {
+    "extract": 10 + 16,   # key bytes in, 16-byte tuple out
+    "pass": 16 + 16,      # tuple in, tuple out, per level that moves it
+    "hist": 16,           # tuple in
+    "finish": 16 + 4,     # tuple in, u32 permutation out
+    "gather": 4 + 100 + 100,  # permutation + record in, record out
+}
+PATH_BYTES = 314          # whole path: extract + 2 passes + finish + gather
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_08006_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x: float, pg, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+# ----------------------------------------------------------- CPU baseline
+
+def oracle_sample(n_sample: int, seed: int = 2):
+    """The CPU oracle (single-threaded qsort on (key, index) + record copy) on
+    the first n_sample records of the workload.  Returns (GB/s, seconds)."""
+    import datagen
+    import oracle
+    recs = datagen.uniform_records(n_sample, seed=seed).numpy()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.sort_records(recs, key_bytes=KEY)
+    dt = time.perf_counter() - t0
+    return n_sample * REC / dt / 1e9, dt
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = args.n
+    stream = torch.cuda.Stream(dev)
+    d_in = datagen.uniform_records(n, seed=2, device=dev)
+    d_out = torch.empty_like(d_in)
+    torch.cuda.synchronize()
+
+    def step():
+        ley.ley_sort_records(d_in, d_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error during warm-up")
+
+    # ---- timed region (device time on the sorting stream)
+    clk = ClockSampler(dev.index)
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    launches0 = ley.ley_launch_count()
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = ley.ley_launch_count() - launches0
+    barrier(pg, dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, pg, dev)
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error in the timed region")
+
+    # ---- per-kernel times (events around each launch, same stream)
+    ley.ley_profile_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    prof = ley.ley_profile_read()
+    ley.ley_profile_enable(False)
+    peak, peak_src = load_peaks()
+    kernels = {}
+    for name, (cnt, tot) in prof.items():
+        per_sort_ms = tot / 3
+        entry = {"launches_per_sort": cnt // 3, "ms_per_sort": round(per_sort_ms, 4)}
+        if name in ALG_BYTES:
+            moved = ALG_BYTES[name] * n * (2 if name == "pass" else 1)
+            entry["alg_GBps"] = round(moved / (per_sort_ms * 1e-3) / 1e9, 1)
+        kernels[name] = entry
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    dom_ms = prof[dom][1] / 3
+    dom_bytes = ALG_BYTES.get(dom, 0) * n * (2 if dom == "pass" else 1)
+    dom_launch_ms = prof[dom][1] / prof[dom][0]
+    # the dominant kernel moves its bytes in one launch (gather) or in the
+    # launches that carry work (pass: two levels at uniform keys)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    workload = f"uniform_{n}"
+    roofline = {
+        "kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+        "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+        "alg_bytes_per_record": ALG_BYTES.get(dom), "launch_ms": round(dom_launch_ms, 4),
+        "traffic": committed_traffic(dom, workload),
+        "path_frac": round(PATH_BYTES * n / (ms * 1e-3) / 1e9 / peak, 4),
+    }
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        del d_out
+        h_in = d_in.cpu().pin_memory()
+        del d_in
+        torch.cuda.empty_cache()
+        h_out = torch.empty_like(h_in).pin_memory()
+        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+        barrier(pg, dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        dt = max_over_ranks(dt, pg, dev)
+        e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": n * REC,
+               "d2h_bytes_per_step": n * REC}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt = oracle_sample(args.cpu_sample)
+        cpu = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_sample} records of the workload, "
+                         f"single-threaded qsort + record copy, {dt:.1f} s"}
+
+    value = world * n * REC / (ms * 1e-3) / 1e9
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded SplitMix64 records shaped like the paper's gensort data)",
+        "config": {"workload": workload, "records": n, "record_bytes": REC, "key_bytes": KEY,
+                   "resident": "HBM", "l2": "inputs larger than L2 (10 GB), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
+        "cpu_baseline": cpu, "kernels": kernels,
+    }
+
+
+# ------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank, pg):
+    """The oracle, as it stands, on the host cores: each step sorts a bounded
+    sample of the same workload (the paper's system is CPU code with no GPU
+    path; the oracle is this project's CPU statement of the same sort)."""
+    if rank != 0:
+        return None
+    import datagen
+    import oracle
+    oracle.build()
+    recs = datagen.uniform_records(args.ref_sample, seed=2).numpy()
+    for _ in range(args.warmup):
+        oracle.sort_records(recs, key_bytes=KEY)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort_records(recs, key_bytes=KEY)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = args.ref_sample * REC / dt / 1e9
+    sample = (f"first {args.ref_sample} records of the workload per step, "
+              "single-threaded qsort on (key, index) + record copy")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"uniform_{args.n}", "records": args.n, "record_bytes": REC,
+                   "key_bytes": KEY},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=100_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank, pg)
+    else:
+        out = run_ours(args, world, rank, local, pg)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

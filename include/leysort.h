@@ -1,0 +1,137 @@
+/*
+ * leysort -- GPU record sort (C ABI).
+ *
+ * Sorts fixed-size records by a fixed-size key prefix, following the problem
+ * statement of Leyenda (arXiv 1909.08006): Section 1 and Section 4.1 fix the
+ * workload (100-byte records, a 10-byte key, 90-byte value; data sets that fit,
+ * partly fit, or do not fit a memory limit), Section 3.1 / Algorithm 1 the
+ * method (adaptive MSD radix partitioning with small- and tiny-bucket
+ * finishing), Section 3.2 the (key, pointer) tuples, the record scatter and the
+ * external sort-merge pipeline.
+ *
+ * Order: keys compare as unsigned byte strings, byte 0 most significant.  Equal
+ * keys keep their input order (the sort is stable), so the output is unique:
+ * out[j] = in[p(j)] with (key(p(j)), p(j)) strictly increasing.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are plain device or host addresses; sizes are element counts.
+ *  - `stream` is a cudaStream_t (the CUstream handle) passed as void*; NULL is
+ *    the legacy default stream.
+ *  - Device buffers must be 16-byte aligned.  Inputs are never written.
+ *    Output buffers must not overlap inputs.
+ *  - The caller owns all buffers it passes.  The library allocates its own
+ *    scratch stream-ordered (cudaMallocAsync on `stream`) and frees it before
+ *    the call's work ends; every scratch byte counts against `mem_budget`
+ *    (0 = no cap).
+ *  - Errors found on the host are returned before any work is queued.  Errors
+ *    found by a kernel (a bounded wait that gave up) are latched in a
+ *    per-device status word read by ley_last_device_status().
+ */
+#ifndef LEYSORT_H
+#define LEYSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LEY_OK = 0,
+    LEY_EINVAL = 1,       /* bad argument: NULL, misaligned, overlap, mixed memory kinds */
+    LEY_ENOMEM = 2,       /* scratch would exceed mem_budget, or an allocation failed */
+    LEY_EUNSUPPORTED = 3, /* geometry outside the supported range */
+    LEY_ECUDA = 4,        /* a CUDA runtime call failed */
+    LEY_ETIMEOUT = 5      /* a kernel's bounded wait gave up (device-side status) */
+} ley_status;
+
+typedef void* ley_stream_t;
+
+/*
+ * Sort n records of rec_bytes bytes by their first key_bytes bytes.
+ * (Algorithm 1 and Section 3.1; the (key, pointer) tuples and record scatter
+ * of Section 3.2; geometry of Section 4.1.)
+ *
+ *   in, out     n * rec_bytes bytes each, records back to back (array of
+ *               structs).  Both on the device: the internal sort, queued on
+ *               `stream` and asynchronous.  Both in pinned host memory
+ *               (cudaHostAlloc / cudaHostRegister): the partially in-memory
+ *               sort when the input plus scratch fits mem_budget, else the
+ *               external run-formation + k-way merge sort; these block until
+ *               the sorted records are in `out`.  Any other combination
+ *               (mixed, pageable host memory) is LEY_EINVAL.
+ *   rec_bytes   4..4096, a multiple of 4 (100 takes the specialised kernels).
+ *   key_bytes   1..12 and <= rec_bytes; the key is at offset 0.
+ *   mem_budget  cap on the library's device allocations in bytes, 0 = none.
+ *   n           < 2^32.  n == 0 returns LEY_OK without touching the buffers.
+ */
+ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                            uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream);
+
+/*
+ * Sort (key, payload) pairs: keys_in[i] as unsigned 64-bit, ties by input
+ * position i; idx_in[i] travels with its key.  This is the key-pointer sort of
+ * Section 3.2 (and the prefix/pointer pairs of Section 2.1) without a record
+ * gather.  All four arrays on the device, n elements each, asynchronous on
+ * `stream`.  keys_out/idx_out must not overlap the inputs.
+ */
+ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
+                               uint64_t* keys_out, uint32_t* idx_out, uint64_t n,
+                               uint64_t mem_budget, ley_stream_t stream);
+
+/*
+ * One round of Algorithm 1 (Section 3.1, "Cache Aware Scattering Process"):
+ * the histogram of key byte `digit` and the stable partition of the records
+ * into the 256 buckets of that byte.
+ *   order_out  device, n x u32: order_out[j] = input index of the record that
+ *              the partition places at position j (buckets in byte order,
+ *              input order inside a bucket).
+ *   hist_out   device, 256 x u64: bucket sizes.
+ * digit < key_bytes.  Device `in` only.  Asynchronous on `stream`.
+ */
+ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
+                                 uint32_t key_bytes, uint32_t digit, uint32_t* order_out,
+                                 uint64_t* hist_out, ley_stream_t stream);
+
+/*
+ * Device scratch (bytes) that ley_sort_records would allocate for an internal
+ * sort of n records of this geometry.  Host-only; needs no GPU.
+ */
+ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                               uint64_t* bytes);
+
+/* Static English text for a status code (never NULL). */
+const char* ley_status_string(ley_status s);
+
+/*
+ * Waits for `stream`, then returns and clears the device-side status of the
+ * current device: LEY_ETIMEOUT if any kernel's bounded wait gave up since the
+ * last call, LEY_ECUDA if the stream reports an error, else LEY_OK.
+ */
+ley_status ley_last_device_status(ley_stream_t stream);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t ley_launch_count(void);
+
+/*
+ * Per-kernel timing for tracing (Table 3 style per-phase times).  While
+ * enabled, every launch of the library is bracketed by CUDA events on its
+ * stream.  ley_profile_read() waits for those events and fills up to `max`
+ * entries {name, launches, total milliseconds} summed since the last
+ * ley_profile_enable(1); it returns the number of kernel names seen.
+ */
+typedef struct {
+    const char* name;
+    uint64_t launches;
+    double total_ms;
+} ley_kernel_time;
+
+ley_status ley_profile_enable(int on);
+int ley_profile_read(ley_kernel_time* out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEYSORT_H */

@@ -1,0 +1,190 @@
+"""leysort: GPU record sort for one GB300 (sm_103a), a re-design of the
+data-parallel hot path of Leyenda (arXiv 1909.08006).
+
+This module is a thin ctypes binding of the C ABI in ``include/leysort.h``
+(``libleysort.so``): it marshals arguments and nothing else.  Every step of a
+sort runs in the library's CUDA kernels; there is no CPU fallback, and the
+import fails loudly when the library has not been built.
+
+Functions keep the C names.  Buffers may be given as torch tensors (device or
+pinned host memory; PyTorch is used for memory and streams only) or as raw
+integer addresses.  A non-OK status raises :class:`LeyError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "LeyError", "LEY_OK", "LEY_EINVAL", "LEY_ENOMEM", "LEY_EUNSUPPORTED", "LEY_ECUDA",
+    "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
+    "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
+    "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
+]
+
+LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
+
+
+class LeyError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {ley_status_string(status)} (status {status})")
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"libleysort.so is not built ({path}); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    lib.ley_sort_records.argtypes = [vp, vp, u64, u32, u32, u64, vp]
+    lib.ley_sort_records.restype = ctypes.c_int
+    lib.ley_sort_keys_index.argtypes = [vp, vp, vp, vp, u64, u64, vp]
+    lib.ley_sort_keys_index.restype = ctypes.c_int
+    lib.ley_partition_records.argtypes = [vp, u64, u32, u32, u32, vp, vp, vp]
+    lib.ley_partition_records.restype = ctypes.c_int
+    lib.ley_workspace_bytes.argtypes = [u64, u32, u32, ctypes.POINTER(u64)]
+    lib.ley_workspace_bytes.restype = ctypes.c_int
+    lib.ley_status_string.argtypes = [ctypes.c_int]
+    lib.ley_status_string.restype = ctypes.c_char_p
+    lib.ley_last_device_status.argtypes = [vp]
+    lib.ley_last_device_status.restype = ctypes.c_int
+    lib.ley_launch_count.argtypes = []
+    lib.ley_launch_count.restype = u64
+    lib.ley_profile_enable.argtypes = [ctypes.c_int]
+    lib.ley_profile_enable.restype = ctypes.c_int
+    lib.ley_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
+    lib.ley_profile_read.restype = ctypes.c_int
+    return lib
+
+
+class _Lazy:
+    """Loads libleysort.so on first use; raises ImportError if it is not built."""
+
+    _h = None
+
+    def __getattr__(self, name):
+        if _Lazy._h is None:
+            _Lazy._h = _load()
+        return getattr(_Lazy._h, name)
+
+
+_lib = _Lazy()
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding resolves."""
+    return [n for n in __all__ if n.startswith("ley_")]
+
+
+# ----------------------------------------------------------- marshalling
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to leysort must be contiguous")
+        return int(x.data_ptr())
+    raise TypeError(f"expected a tensor or an address, got {type(x).__name__}")
+
+
+def _stream(stream, *tensors) -> int:
+    if stream is not None:
+        return stream if isinstance(stream, int) else int(stream.cuda_stream)
+    for t in tensors:
+        if hasattr(t, "is_cuda") and t.is_cuda:
+            import torch
+            return int(torch.cuda.current_stream(t.device).cuda_stream)
+    return 0
+
+
+def _check(status: int, where: str) -> int:
+    if status != LEY_OK:
+        raise LeyError(status, where)
+    return status
+
+
+def ley_sort_records(inp, out, n: int | None = None, rec_bytes: int | None = None,
+                     key_bytes: int = 10, mem_budget: int = 0, stream=None) -> int:
+    """Sort records (rows of a uint8 [n, rec_bytes] tensor) by their first
+    ``key_bytes`` bytes; see ``ley_sort_records`` in include/leysort.h."""
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
+    st = _lib.ley_sort_records(_addr(inp), _addr(out), n, rec_bytes, key_bytes, mem_budget,
+                               _stream(stream, inp, out))
+    return _check(st, "ley_sort_records")
+
+
+def ley_sort_keys_index(keys_in, idx_in, keys_out, idx_out, n: int | None = None,
+                        mem_budget: int = 0, stream=None) -> int:
+    """Sort (u64 key, u32 payload) pairs by (key, input position)."""
+    if n is None:
+        n = int(keys_in.shape[0])
+    st = _lib.ley_sort_keys_index(_addr(keys_in), _addr(idx_in), _addr(keys_out),
+                                  _addr(idx_out), n, mem_budget,
+                                  _stream(stream, keys_in, keys_out))
+    return _check(st, "ley_sort_keys_index")
+
+
+def ley_partition_records(inp, digit: int, order_out, hist_out, n: int | None = None,
+                          rec_bytes: int | None = None, key_bytes: int = 10, stream=None) -> int:
+    """One radix round: histogram of key byte ``digit`` and the stable
+    partition order (u32 per record, 256 u64 bucket sizes)."""
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1])
+    st = _lib.ley_partition_records(_addr(inp), n, rec_bytes, key_bytes, digit,
+                                    _addr(order_out), _addr(hist_out),
+                                    _stream(stream, inp, order_out))
+    return _check(st, "ley_partition_records")
+
+
+def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10) -> int:
+    v = ctypes.c_uint64(0)
+    _check(_lib.ley_workspace_bytes(n, rec_bytes, key_bytes, ctypes.byref(v)),
+           "ley_workspace_bytes")
+    return int(v.value)
+
+
+def ley_status_string(status: int) -> str:
+    return _lib.ley_status_string(int(status)).decode()
+
+
+def ley_last_device_status(stream=None) -> int:
+    """Waits for the stream; returns (does not raise) the device-side status."""
+    return int(_lib.ley_last_device_status(_stream(stream)))
+
+
+def ley_launch_count() -> int:
+    return int(_lib.ley_launch_count())
+
+
+def ley_profile_enable(on: bool = True) -> int:
+    return _check(_lib.ley_profile_enable(1 if on else 0), "ley_profile_enable")
+
+
+def ley_profile_read(max_entries: int = 64) -> dict[str, tuple[int, float]]:
+    """{kernel name: (launches, total ms)} since profiling was enabled."""
+    arr = (_KernelTime * max_entries)()
+    k = _lib.ley_profile_read(arr, max_entries)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(k, max_entries))}

@@ -1,0 +1,44 @@
+// Launch wrappers of the leysort kernels (host-side declarations).
+#pragma once
+
+#include "ley_internal.cuh"
+
+namespace ley {
+
+struct LaunchCfg {
+    int grid;
+    int block;
+    size_t smem;
+    cudaStream_t stream;
+};
+
+// Records -> tuples, histogram of key byte `hist_digit`, key-difference mask
+// of the whole input (list 0, slot 0).
+cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, unsigned long long n,
+                                   uint32_t rec_bytes, KeySpec ks, const Work& w, int hist_digit);
+cudaError_t launch_extract_pairs(const LaunchCfg& c, const uint64_t* keys, const uint32_t* idx,
+                                 unsigned long long n, KeySpec ks, const Work& w);
+cudaError_t launch_init(cudaStream_t s, const Work& w, unsigned long long n, int digit0);
+cudaError_t launch_hist(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
+cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
+cudaError_t launch_classify_partition(cudaStream_t s, const Work& w);
+cudaError_t launch_pass(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
+cudaError_t launch_finish_records(const LaunchCfg& c, const Work& w, KeySpec ks);
+cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, uint64_t* keys_out,
+                                uint32_t* idx_out);
+cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
+                          const uint32_t* perm, unsigned long long n, uint32_t rec_bytes,
+                          int variant);
+cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsigned long long n,
+                                 uint32_t* order_out, unsigned long long* hist_out);
+
+// Occupancy-derived persistent grid sizes (blocks per SM) for a kernel kind.
+enum KernelKind {
+    KK_EXTRACT_REC = 0, KK_EXTRACT_PAIRS, KK_HIST, KK_PASS, KK_FINISH_REC, KK_FINISH_PAIRS,
+    KK_GATHER100, KK_GATHER100_TMA, KK_GATHER_GENERIC, KK_COUNT
+};
+int blocks_per_sm(KernelKind k);
+size_t kernel_smem(KernelKind k);
+int kernel_threads(KernelKind k);
+
+}  // namespace ley

@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every entry point its header declares
+(host-only checks, no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "leysort.h")
+
+
+@pytest.fixture(scope="module")
+def ley():
+    from paper_1909_08006_gb300 import build
+    build.build()
+    import paper_1909_08006_gb300 as m
+    return m
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ley_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
+                     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ley):
+    lib = ctypes.CDLL(ley.library_path())
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in leysort.h but not exported"
+    for name in ley.exported_symbols():
+        assert name in declared_functions(), f"binding names {name}, header does not"
+
+
+def test_host_only_entry_points(ley):
+    assert ley.ley_status_string(ley.LEY_OK) == "ok"
+    assert "budget" in ley.ley_status_string(ley.LEY_ENOMEM)
+    assert ley.ley_status_string(99) == "unknown status"
+    assert ley.ley_workspace_bytes(0) == 0
+    b = ley.ley_workspace_bytes(100_000_000)
+    # two 16-byte tuple buffers + a 4-byte permutation per record, plus control
+    assert 36 * 100_000_000 < b < 42 * 100_000_000
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_workspace_bytes(10, rec_bytes=100, key_bytes=13)
+    assert e.value.status == ley.LEY_EUNSUPPORTED
+    with pytest.raises(ley.LeyError):
+        ley.ley_workspace_bytes(10, rec_bytes=102, key_bytes=10)
+
+
+def test_argument_checks_before_any_gpu_work(ley):
+    # geometry and size checks happen before memory kinds are inspected
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_sort_records(0, 0, n=10, rec_bytes=100, key_bytes=0)
+    assert e.value.status == ley.LEY_EUNSUPPORTED
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_sort_records(0, 0, n=1 << 32, rec_bytes=100, key_bytes=10)
+    assert e.value.status == ley.LEY_EUNSUPPORTED
+    # n == 0 is a no-op that touches nothing
+    assert ley.ley_sort_records(0, 0, n=0, rec_bytes=100, key_bytes=10) == ley.LEY_OK
+    assert ley.ley_sort_keys_index(0, 0, 0, 0, n=0) == ley.LEY_OK
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_sort_records(0, 0, n=5, rec_bytes=100, key_bytes=10)
+    assert e.value.status == ley.LEY_EINVAL
+
+
+def test_launch_counter_and_profiler_are_host_state(ley):
+    assert ley.ley_launch_count() >= 0
+    ley.ley_profile_enable(True)
+    assert ley.ley_profile_read() == {}
+    ley.ley_profile_enable(False)
