@@ -100,7 +100,8 @@ static cudaError_t launch(const char* name, cudaStream_t s, F&& f) {
 // ---------------------------------------------------------------- layout
 
 struct Layout {
-    size_t tup[2], perm, ctl, segs[2], stb[2], hist[2], diff[2], pslot, ptb, bb, fin, status;
+    size_t tup[2], perm, ctl, segs[2], stb[2], sto[2], hist[2], diff[2], pslot, ptb, pto, bb, fin,
+        status;
     size_t total;
     ull cap_seg, cap_fin, cap_tiles;
 };
@@ -125,11 +126,13 @@ static Layout make_layout(ull n, bool with_perm) {
     for (int p = 0; p < 2; p++) {
         L.segs[p] = put(L.cap_seg * sizeof(Seg));
         L.stb[p] = put(L.cap_seg * sizeof(uint32_t));
+        L.sto[p] = put(L.cap_tiles * sizeof(uint32_t));
         L.hist[p] = put(L.cap_seg * kRadix * sizeof(uint32_t));
         L.diff[p] = put(L.cap_seg * sizeof(Diff));
     }
     L.pslot = put(L.cap_seg * sizeof(uint32_t));
     L.ptb = put(L.cap_seg * sizeof(uint32_t));
+    L.pto = put(L.cap_tiles * sizeof(uint32_t));
     L.bb = put(L.cap_seg * kRadix * sizeof(uint32_t));
     L.fin = put(L.cap_fin * sizeof(FinTask));
     L.status = put(L.cap_tiles * kRadix * sizeof(ull));
@@ -146,11 +149,13 @@ static Work make_work(char* base, const Layout& L, ull n, uint32_t* err) {
     for (int p = 0; p < 2; p++) {
         w.segs[p] = reinterpret_cast<Seg*>(base + L.segs[p]);
         w.seg_tile_base[p] = reinterpret_cast<uint32_t*>(base + L.stb[p]);
+        w.seg_tile_owner[p] = reinterpret_cast<uint32_t*>(base + L.sto[p]);
         w.hist[p] = reinterpret_cast<uint32_t*>(base + L.hist[p]);
         w.diff[p] = reinterpret_cast<Diff*>(base + L.diff[p]);
     }
     w.pass_slot = reinterpret_cast<uint32_t*>(base + L.pslot);
     w.pass_tile_base = reinterpret_cast<uint32_t*>(base + L.ptb);
+    w.pass_tile_owner = reinterpret_cast<uint32_t*>(base + L.pto);
     w.bucket_base = reinterpret_cast<uint32_t*>(base + L.bb);
     w.fin = reinterpret_cast<FinTask*>(base + L.fin);
     w.status = reinterpret_cast<ull*>(base + L.status);
@@ -178,10 +183,12 @@ static KeySpec pair_keyspec() {
     return ks;
 }
 
+// Record gather kernel: TMA bulk copies (default) or plain vector loads
+// (LEY_GATHER=lsu), kept for comparison.
 static int gather_variant() {
     const char* v = std::getenv("LEY_GATHER");
-    if (v && std::strcmp(v, "tma") == 0) return 1;
-    return 0;
+    if (v && std::strcmp(v, "lsu") == 0) return 0;
+    return 1;
 }
 
 // ----------------------------------------------------- the internal sort
@@ -239,7 +246,7 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
         }));
         return LEY_OK;
     }
-    const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kPassThreads, 0, st};
+    const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
     const LaunchCfg cc{2 * sms, 128, 0, st};
     for (int lvl = 0; lvl < ks.ndig; lvl++) {
         if (lvl > 0) LEY_TRY(launch("hist", st, [&] { return launch_hist(ch, w, ks, lvl); }));

@@ -20,17 +20,27 @@ constexpr int kRadix = 256;
 constexpr int kMaxDigits = 12;      // key bytes a tuple can hold
 constexpr int kMaxLevels = 12;      // one MSD level per digit at most
 
-// Tile of the multi-CTA passes (histogram and scatter): 256 threads x 16.
-constexpr int kPassThreads = 256;
-constexpr int kPassItems = 16;
-constexpr int kPassTile = kPassThreads * kPassItems;   // 4096 tuples
+// Tile of the multi-CTA passes (histogram and scatter): 4096 tuples.  The
+// scatter pass uses 512 threads x 8 items, the histogram 256 threads x 16.
+constexpr int kPassTile = 4096;
+constexpr int kPassThreads = 512;
+constexpr int kPassItems = kPassTile / kPassThreads;   // 8
+constexpr int kPassWarps = kPassThreads / 32;          // 16
+constexpr int kHistThreads = 256;
+constexpr int kHistItems = kPassTile / kHistThreads;   // 16
 
 // In-CTA finishing (the small-bucket queue of Algorithm 1): 256 threads x 8.
 constexpr int kFinThreads = 256;
+constexpr int kFinWarps = kFinThreads / 32;
 constexpr int kFinItems = 8;
-constexpr int kSmall = kFinThreads * kFinItems;        // 2048 tuples
-constexpr int kTiny = 32;                              // comparison-rank cutoff
-constexpr int kFinStack = kSmall / (kTiny + 1) + 2;
+constexpr int kSmall = kFinThreads * kFinItems;        // 2048 tuples: big-bucket threshold
+constexpr int kTiny = 32;                              // tiny-bucket threshold (comparison rank)
+constexpr int kWarpMax = 32 * kFinItems;               // sub-buckets one warp sorts (256)
+// Sub-buckets above kTiny inside one task are disjoint at each digit depth,
+// so at most kSmall / (kTiny + 1) per depth and kMaxDigits depths: the
+// queue never needs more slots than this and never wraps.
+constexpr int kFinQueue = (kSmall / (kTiny + 1)) * 12 + 8;   // 752
+constexpr int kFinStack = kSmall / (kWarpMax + 1) + 2;       // block stack (> kWarpMax)
 
 // Device-side error bits (latched in the per-device status word).
 constexpr uint32_t kErrTimeout = 1u;
@@ -101,8 +111,10 @@ struct Work {
     uint32_t* seg_tile_base[2];
     uint32_t* hist[2];            // [cap_seg][256]
     Diff* diff[2];
+    uint32_t* seg_tile_owner[2];  // tile -> slot in the big list
     uint32_t* pass_slot;          // pass entry -> slot in list
     uint32_t* pass_tile_base;
+    uint32_t* pass_tile_owner;    // pass tile -> pass entry
     uint32_t* bucket_base;        // [cap_seg][256] exclusive offsets
     FinTask* fin;
     unsigned long long* status;   // [cap_tiles][256] look-back words
@@ -110,6 +122,24 @@ struct Work {
     unsigned long long cap_seg, cap_fin, cap_tiles;
     unsigned long long n;
 };
+
+// Optional per-phase cycle counters for tracing kernel internals; compiled
+// in only with -DLEY_PHASE_TIMING (never in the library build).  Thread 0 of
+// each CTA adds the cycles since its previous mark to counter k.
+#ifdef LEY_PHASE_TIMING
+#define LEY_PHASE_BEGIN long long ley_tp_ = clock64()
+#define LEY_PHASE(k)                                                             \
+    do {                                                                         \
+        if (threadIdx.x == 0) {                                                  \
+            long long t_ = clock64();                                            \
+            atomicAdd(&g_ley_phase[k], (unsigned long long)(t_ - ley_tp_));      \
+            ley_tp_ = t_;                                                        \
+        }                                                                        \
+    } while (0)
+#else
+#define LEY_PHASE_BEGIN
+#define LEY_PHASE(k)
+#endif
 
 __host__ __device__ inline uint32_t ceil_div_u64(unsigned long long a, unsigned long long b) {
     return (uint32_t)((a + b - 1) / b);

@@ -24,6 +24,10 @@ namespace ley {
 
 using ull = unsigned long long;
 
+#ifdef LEY_PHASE_TIMING
+__device__ unsigned long long g_ley_phase[64];
+#endif
+
 // ------------------------------------------------------------- helpers
 
 __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
@@ -68,16 +72,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Largest i in [0, cnt) with base[i] <= t (base is non-decreasing, base[0] = 0).
-__device__ __forceinline__ uint32_t find_owner(const uint32_t* base, uint32_t cnt, uint32_t t) {
-    uint32_t lo = 0, hi = cnt;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (base[mid] <= t) lo = mid; else hi = mid;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ uint32_t sel8(const uint32_t (&w)[8], uint32_t q) {
@@ -131,12 +125,45 @@ __device__ __forceinline__ void flush_diff(const uint32_t* sh3, Diff* g) {
     if (sh3[2]) atomicOr(&g->lo, sh3[2]);
 }
 
-// Histogram update with warp-level aggregation: lanes holding the same digit
-// elect one leader that adds the group's size (digit 256 = no item).
-__device__ __forceinline__ void hist_add_warp(uint32_t* sh_hist, uint32_t dg) {
-    uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    if (dg < 256u && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1))
-        atomicAdd(&sh_hist[dg], (uint32_t)__popc(peers));
+// Histogram update with warp-level ballot aggregation: the lanes whose digit
+// equals lane 0's add their count in one shared-memory atomic, the others
+// add one each (digit 256 = no item).
+__device__ __forceinline__ void hist_add_vote(uint32_t* sh_hist, uint32_t dg) {
+    const uint32_t first = __shfl_sync(0xffffffffu, dg, 0);
+    const uint32_t same = __ballot_sync(0xffffffffu, dg == first);
+    if (dg == first) {
+        if ((threadIdx.x & 31) == 0 && dg < 256u) atomicAdd(&sh_hist[dg], (uint32_t)__popc(same));
+    } else if (dg < 256u) {
+        atomicAdd(&sh_hist[dg], 1u);
+    }
+}
+
+// Lanes of the warp whose 8-bit digit equals this lane's (multi-split by
+// eight ballots, one per digit bit).
+__device__ __forceinline__ uint32_t peers8(uint32_t dg) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const bool bit = (dg >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+
+// Stable rank of this lane's item among the warp's items with the same digit
+// so far: counter value before this step (returned by the group leader's
+// shared-memory atomic, broadcast by shuffle) plus the lower lanes of the
+// group.  Successive calls of a warp see its counters in program order.
+__device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool valid,
+                                              uint32_t lt_mask, int lane) {
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    const uint32_t peers = peers8(dg) & vmask;
+    const int leader = valid ? __ffs(peers) - 1 : lane;
+    uint32_t old = 0;
+    if (valid && lane == leader) old = atomicAdd(&cnt[dg], (uint32_t)__popc(peers));
+    old = __shfl_sync(0xffffffffu, old, leader);
+    return old + __popc(peers & lt_mask);
 }
 
 // ------------------------------------------------------------- extract
@@ -177,7 +204,7 @@ k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpe
                 dhi |= key_hi(t[u]) ^ key_hi(ref);
                 dlo |= t[u].z ^ ref.z;
             }
-            hist_add_warp(sh_hist, dg);
+            hist_add_vote(sh_hist, dg);
         }
     }
     warp_or_diff(dhi, dlo, sh_d);
@@ -216,7 +243,7 @@ k_extract_pairs(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
                 dg = (uint32_t)(k[u] >> 56);
                 dhi |= k[u] ^ ref;
             }
-            hist_add_warp(sh_hist, dg);
+            hist_add_vote(sh_hist, dg);
         }
     }
     warp_or_diff(dhi, 0u, sh_d);
@@ -241,7 +268,7 @@ __global__ void k_init(Work w, ull n, int digit0) {
 
 // ------------------------------------------------------------ histogram
 
-__global__ void __launch_bounds__(kPassThreads)
+__global__ void __launch_bounds__(kHistThreads)
 k_hist(Work w, KeySpec ks, int L) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
@@ -251,7 +278,7 @@ k_hist(Work w, KeySpec ks, int L) {
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
     const uint32_t ntiles = (uint32_t)(packed & kPackMask);
     const int tid = threadIdx.x;
-    if (nseg > w.cap_seg) {  // an append overflowed: the list is not usable
+    if (nseg > w.cap_seg || ntiles > w.cap_tiles) {  // an append overflowed
         if (tid == 0 && blockIdx.x == 0) atomicOr(w.err, kErrCapacity);
         return;
     }
@@ -263,33 +290,33 @@ k_hist(Work w, KeySpec ks, int L) {
         __syncthreads();
         const uint32_t t = sh_tile;
         if (t >= ntiles) break;
-        const uint32_t s = find_owner(w.seg_tile_base[p], nseg, t);
+        const uint32_t s = w.seg_tile_owner[p][t];
         const Seg sg = w.segs[p][s];
+        if (s >= nseg || sg.start + sg.count > w.n || t < w.seg_tile_base[p][s] || sg.buf > 1) {
+            if (tid == 0) atomicOr(w.err, kErrCapacity);  // never for a valid list
+            continue;
+        }
         const uint32_t lt = t - w.seg_tile_base[p][s];
         const ull base = sg.start + (ull)lt * kPassTile;
         const uint32_t m = min((uint32_t)kPassTile, sg.count - lt * (uint32_t)kPassTile);
         const uint4* src = w.tup[sg.buf];
         const uint4 ref = src[sg.start];
-        uint4 v[kPassItems];
+        uint4 v[kHistItems];
 #pragma unroll
-        for (int k = 0; k < kPassItems; k++) {
-            uint32_t idx = k * kPassThreads + tid;
-            v[k] = idx < m ? src[base + idx] : make_uint4(0, 0, 0, 0);
+        for (int k = 0; k < kHistItems; k++) {
+            uint32_t idx = k * kHistThreads + tid;
+            v[k] = idx < m ? src[base + idx] : ref;
         }
         ull dhi = 0;
         uint32_t dlo = 0;
 #pragma unroll
-        for (int k = 0; k < kPassItems; k++) {
-            uint32_t idx = k * kPassThreads + tid;
-            uint32_t dg = 256u;
-            if (idx < m) {
-                dg = digit_of(v[k], sg.digit);
-                dhi |= key_hi(v[k]) ^ key_hi(ref);
-                dlo |= (v[k].z ^ ref.z) & ks.lo_mask;
-            }
-            hist_add_warp(sh_hist, dg);
+        for (int k = 0; k < kHistItems; k++) {
+            uint32_t idx = k * kHistThreads + tid;
+            dhi |= key_hi(v[k]) ^ key_hi(ref);
+            dlo |= v[k].z ^ ref.z;
+            hist_add_vote(sh_hist, idx < m ? digit_of(v[k], sg.digit) : 256u);
         }
-        warp_or_diff(dhi & ks.hi_mask, dlo, sh_d);
+        warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, sh_d);
         __syncthreads();
         if (sh_hist[tid]) atomicAdd(&w.hist[p][(ull)s * kRadix + tid], sh_hist[tid]);
         if (tid == 0) flush_diff(sh_d, &w.diff[p][s]);
@@ -313,115 +340,205 @@ __device__ void emit_fin(const Work& w, ull start, uint32_t count, int digit, in
     w.fin[slot] = f;
 }
 
-__device__ void append_big(const Work& w, int L1, ull start, uint32_t count, int digit, int buf) {
-    const int q = L1 & 1;
-    ull pk = atomicAdd(&w.ctl->lvl[L1].big_packed,
-                       (1ull << kPackShift) | (ull)ceil_div_u64(count, kPassTile));
-    ull slot = pk >> kPackShift;
-    if (slot >= w.cap_seg) {
-        atomicOr(w.err, kErrCapacity);
+// Appends a bucket to the next level's big list (called by a whole warp with
+// the same arguments): its slot and first tile come from one 64-bit atomic,
+// so slots and tiles are numbered in the same order; the lanes fill the
+// tile-owner table and clear the bucket's histogram.
+__device__ void append_big_warp(const Work& w, int L1, ull start, uint32_t count, int digit,
+                                int buf) {
+    const int q = L1 & 1, lane = threadIdx.x & 31;
+    const uint32_t nt = ceil_div_u64(count, kPassTile);
+    ull pk = 0;
+    if (lane == 0) pk = atomicAdd(&w.ctl->lvl[L1].big_packed, (1ull << kPackShift) | (ull)nt);
+    pk = __shfl_sync(0xffffffffu, pk, 0);
+    const ull slot = pk >> kPackShift;
+    const ull tb = pk & kPackMask;
+    if (slot >= w.cap_seg || tb + nt > w.cap_tiles) {
+        if (lane == 0) atomicOr(w.err, kErrCapacity);
         return;
     }
-    Seg s;
-    s.start = start;
-    s.count = count;
-    s.digit = (uint16_t)digit;
-    s.buf = (uint8_t)buf;
-    s.pad = 0;
-    w.segs[q][slot] = s;
-    w.seg_tile_base[q][slot] = (uint32_t)(pk & kPackMask);
+    if (lane == 0) {
+        Seg sg;
+        sg.start = start;
+        sg.count = count;
+        sg.digit = (uint16_t)digit;
+        sg.buf = (uint8_t)buf;
+        sg.pad = 0;
+        w.segs[q][slot] = sg;
+        w.seg_tile_base[q][slot] = (uint32_t)tb;
+        Diff z;
+        z.hi = 0;
+        z.lo = 0;
+        z.pad = 0;
+        w.diff[q][slot] = z;
+    }
+    for (uint32_t i = lane; i < nt; i += 32) w.seg_tile_owner[q][tb + i] = (uint32_t)slot;
     uint4* h = reinterpret_cast<uint4*>(w.hist[q] + slot * kRadix);
-    for (int i = 0; i < kRadix / 4; i++) h[i] = make_uint4(0, 0, 0, 0);
-    Diff z;
-    z.hi = 0;
-    z.lo = 0;
-    z.pad = 0;
-    w.diff[q][slot] = z;
+    h[lane] = make_uint4(0, 0, 0, 0);
+    h[lane + 32] = make_uint4(0, 0, 0, 0);
 }
 
+// One warp per bucket of level L's big list (Algorithm 1's control flow):
+//  - a bucket of at most kSmall tuples becomes a finishing task;
+//  - a bucket whose current digit is single-valued skips to the first digit
+//    where its keys differ, without moving (or finishes if none is left);
+//  - otherwise it is scattered this level: its sub-buckets above kSmall
+//    recurse on the next digit, runs of smaller ones are packed into
+//    finishing tasks of at most kSmall tuples.
 __global__ void __launch_bounds__(128)
 k_classify(Work w, KeySpec ks, int L) {
-    const int p = L & 1;
+    __shared__ uint32_t sh_cnt[4][kRadix];   // per warp: bin counts
+    __shared__ uint32_t sh_gs[4][kRadix];    // per warp: task start offsets
+    __shared__ uint32_t sh_gc[4][kRadix];    // per warp: count << 1 | single-bucket
+    const int p = L & 1, lane = threadIdx.x & 31;
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
     if (nseg > w.cap_seg) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.err, kErrCapacity);
         return;
     }
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
         const Seg sg = w.segs[p][s];
         if (sg.count <= (uint32_t)kSmall) {
-            emit_fin(w, sg.start, sg.count, sg.digit, sg.buf, 0);
+            if (lane == 0) emit_fin(w, sg.start, sg.count, sg.digit, sg.buf, 0);
             continue;
         }
-        const uint4* h4 = reinterpret_cast<const uint4*>(w.hist[p] + (ull)s * kRadix);
-        int nz = 0;
-        for (int i = 0; i < kRadix / 4; i++) {
-            uint4 c = h4[i];
-            nz += (c.x != 0) + (c.y != 0) + (c.z != 0) + (c.w != 0);
-        }
-        if (nz <= 1) {
-            // The digit is the same across the bucket: skip it without moving
-            // anything, straight to the first digit where keys differ.
-            const Diff df = w.diff[p][s];
-            int d2 = first_varying_digit(df.hi & ks.hi_mask, df.lo & ks.lo_mask, sg.digit + 1,
-                                         ks.ndig);
-            if (d2 >= ks.ndig)
-                emit_fin(w, sg.start, sg.count, ks.ndig, sg.buf, 1);
-            else
-                append_big(w, L + 1, sg.start, sg.count, d2, sg.buf);
-            continue;
-        }
-        ull pk = atomicAdd(&w.ctl->lvl[L].pass_packed,
-                           (1ull << kPackShift) | (ull)ceil_div_u64(sg.count, kPassTile));
-        const uint32_t e = (uint32_t)(pk >> kPackShift);
-        if (e >= w.cap_seg) {
-            atomicOr(w.err, kErrCapacity);
-            continue;
-        }
-        w.pass_slot[e] = s;
-        w.pass_tile_base[e] = (uint32_t)(pk & kPackMask);
-        uint32_t* bb = w.bucket_base + (ull)e * kRadix;
         const uint32_t* h = w.hist[p] + (ull)s * kRadix;
+        uint32_t c8[8], sum = 0;
+        int nz = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            c8[k] = h[lane * 8 + k];
+            sum += c8[k];
+            nz += c8[k] != 0;
+        }
+        nz = __reduce_add_sync(0xffffffffu, (uint32_t)nz);
+        if (nz <= 1) {
+            const Diff df = w.diff[p][s];
+            const int d2 = first_varying_digit(df.hi & ks.hi_mask, df.lo & ks.lo_mask,
+                                               sg.digit + 1, ks.ndig);
+            if (d2 >= ks.ndig) {
+                if (lane == 0) emit_fin(w, sg.start, sg.count, ks.ndig, sg.buf, 1);
+            } else {
+                append_big_warp(w, L + 1, sg.start, sg.count, d2, sg.buf);
+            }
+            continue;
+        }
+        const uint32_t nt = ceil_div_u64(sg.count, kPassTile);
+        ull pk = 0;
+        if (lane == 0) pk = atomicAdd(&w.ctl->lvl[L].pass_packed, (1ull << kPackShift) | (ull)nt);
+        pk = __shfl_sync(0xffffffffu, pk, 0);
+        const uint32_t e = (uint32_t)(pk >> kPackShift);
+        const ull tb = pk & kPackMask;
+        if (e >= w.cap_seg || tb + nt > w.cap_tiles) {
+            if (lane == 0) atomicOr(w.err, kErrCapacity);
+            continue;
+        }
+        if (lane == 0) {
+            w.pass_slot[e] = s;
+            w.pass_tile_base[e] = (uint32_t)tb;
+        }
+        for (uint32_t i = lane; i < nt; i += 32) w.pass_tile_owner[tb + i] = e;
+        // Exclusive scan over the 256 bins (lane l owns bins 8l..8l+7).
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t off8[8], run = incl - sum;
+        uint32_t* bb = w.bucket_base + (ull)e * kRadix;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            off8[k] = run;
+            bb[lane * 8 + k] = run;
+            run += c8[k];
+        }
         const int nb = sg.buf ^ 1;
         const int d1 = sg.digit + 1;
-        uint32_t off = 0, g_start = 0, g_count = 0, g_nb = 0;
-        for (int v = 0; v < kRadix; v++) {
-            const uint32_t c = h[v];
-            bb[v] = off;
-            if (c == 0) continue;
-            if (c > (uint32_t)kSmall) {
-                if (g_count) {
-                    emit_fin(w, sg.start + g_start, g_count, g_nb == 1 ? d1 : sg.digit, nb, 0);
-                    g_count = 0;
-                    g_nb = 0;
-                }
+        // Big sub-buckets recurse: the warp appends them one by one.
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            uint32_t big = __ballot_sync(0xffffffffu, c8[k] > (uint32_t)kSmall);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const uint32_t c = __shfl_sync(0xffffffffu, c8[k], src);
+                const uint32_t o = __shfl_sync(0xffffffffu, off8[k], src);
                 if (d1 < ks.ndig)
-                    append_big(w, L + 1, sg.start + off, c, d1, nb);
-                else
-                    emit_fin(w, sg.start + off, c, ks.ndig, nb, 1);
-            } else {
-                if (g_count && g_count + c > (uint32_t)kSmall) {
-                    emit_fin(w, sg.start + g_start, g_count, g_nb == 1 ? d1 : sg.digit, nb, 0);
+                    append_big_warp(w, L + 1, sg.start + o, c, d1, nb);
+                else if (lane == 0)
+                    emit_fin(w, sg.start + o, c, ks.ndig, nb, 1);
+            }
+        }
+        // Runs of small sub-buckets are packed greedily into finishing tasks
+        // (lane 0 walks the bins in shared memory, the warp then reserves all
+        // task slots with one atomic and writes them).
+        uint32_t* cs = sh_cnt[threadIdx.x >> 5];
+#pragma unroll
+        for (int k = 0; k < 8; k++) cs[lane * 8 + k] = c8[k];
+        __syncwarp();
+        uint32_t ng = 0;
+        if (lane == 0) {
+            uint32_t off = 0, g_start = 0, g_count = 0, g_nb = 0;
+            for (int v = 0; v < kRadix; v++) {
+                const uint32_t c = cs[v];
+                if (c == 0) continue;
+                if (c > (uint32_t)kSmall || (g_count && g_count + c > (uint32_t)kSmall)) {
+                    if (g_count) {
+                        sh_gs[threadIdx.x >> 5][ng] = g_start;
+                        sh_gc[threadIdx.x >> 5][ng] = (g_count << 1) | (g_nb == 1 ? 1u : 0u);
+                        ng++;
+                    }
                     g_count = 0;
                     g_nb = 0;
                 }
-                if (g_count == 0) g_start = off;
-                g_count += c;
-                g_nb++;
+                if (c <= (uint32_t)kSmall) {
+                    if (g_count == 0) g_start = off;
+                    g_count += c;
+                    g_nb++;
+                }
+                off += c;
             }
-            off += c;
+            if (g_count) {
+                sh_gs[threadIdx.x >> 5][ng] = g_start;
+                sh_gc[threadIdx.x >> 5][ng] = (g_count << 1) | (g_nb == 1 ? 1u : 0u);
+                ng++;
+            }
         }
-        if (g_count) emit_fin(w, sg.start + g_start, g_count, g_nb == 1 ? d1 : sg.digit, nb, 0);
+        __syncwarp();  // lane 0's task list is visible to the warp
+        ng = __shfl_sync(0xffffffffu, ng, 0);
+        ull base = 0;
+        if (lane == 0 && ng) base = atomicAdd(&w.ctl->fin_count, (ull)ng);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t i = lane; i < ng; i += 32) {
+            if (base + i >= w.cap_fin) {
+                atomicOr(w.err, kErrCapacity);
+                break;
+            }
+            const uint32_t gc = sh_gc[threadIdx.x >> 5][i];
+            FinTask f;
+            f.start = sg.start + sh_gs[threadIdx.x >> 5][i];
+            f.count = gc >> 1;
+            f.digit = (uint16_t)((gc & 1u) ? d1 : sg.digit);
+            f.buf = (uint8_t)nb;
+            f.flags = 0;
+            w.fin[base + i] = f;
+        }
+        __syncwarp();
     }
 }
 
 // Partition mode (one round of Algorithm 1 only): the single top segment is
 // scattered on its digit whatever its histogram, and nothing recurses.
 __global__ void k_classify_partition(Work w) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const Seg sg = w.segs[0][0];
-    w.ctl->lvl[0].pass_packed = (1ull << kPackShift) | ceil_div_u64(sg.count, kPassTile);
+    const uint32_t nt = ceil_div_u64(sg.count, kPassTile);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x)
+        w.pass_tile_owner[i] = 0;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    w.ctl->lvl[0].pass_packed = (1ull << kPackShift) | nt;
     w.pass_slot[0] = 0;
     w.pass_tile_base[0] = 0;
     uint32_t off = 0;
@@ -441,13 +558,16 @@ __device__ __forceinline__ ull pack_status(ull flag, int epoch, ull val) {
     return flag | ((ull)epoch << 56) | (val & kValMask);
 }
 
+// One scatter pass of Algorithm 1 over every big bucket of level L.  A CTA
+// takes 4096-tuple tiles in order from a counter, so every predecessor of a
+// tile is already running (forward progress of the look-back).
 __global__ void __launch_bounds__(kPassThreads, 2)
 k_pass(Work w, KeySpec ks, int L) {
     extern __shared__ uint4 stage[];                 // kPassTile tuples
-    __shared__ uint16_t wcnt[kPassThreads / 32][kRadix];
+    __shared__ uint32_t wcnt[kPassWarps][kRadix];    // per-warp digit counters
     __shared__ uint32_t loc_off[kRadix];
     __shared__ ull gbase[kRadix];
-    __shared__ uint32_t warp_tot[kPassThreads / 32];
+    __shared__ uint32_t scan_tot[kRadix / 32];
     __shared__ uint32_t sh_tile;
     __shared__ int sh_bad;
 
@@ -462,21 +582,26 @@ k_pass(Work w, KeySpec ks, int L) {
     const int epoch = L + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
-
+    LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
+        LEY_PHASE(0);
         if (tid == 0) {
             sh_tile = atomicAdd(&w.ctl->lvl[L].pass_tile_ctr, 1u);
             sh_bad = 0;
         }
-#pragma unroll
-        for (int ww = 0; ww < kPassThreads / 32; ww++) wcnt[ww][tid] = 0;
+        for (int i = tid; i < kPassWarps * kRadix; i += kPassThreads) (&wcnt[0][0])[i] = 0;
         __syncthreads();
         const uint32_t t = sh_tile;
         if (t >= ntiles) break;
-        const uint32_t e = find_owner(w.pass_tile_base, npass, t);
+        LEY_PHASE(1);
+        const uint32_t e = w.pass_tile_owner[t];
         const uint32_t tile0 = w.pass_tile_base[e];
         const Seg sg = w.segs[p][w.pass_slot[e]];
+        if (e >= npass || sg.start + sg.count > w.n || t < tile0 || sg.buf > 1) {
+            if (tid == 0) atomicOr(w.err, kErrCapacity);  // never for a valid list
+            continue;
+        }
         const uint32_t lt = t - tile0;
         const ull base = sg.start + (ull)lt * kPassTile;
         const uint32_t m = min((uint32_t)kPassTile, sg.count - lt * (uint32_t)kPassTile);
@@ -484,13 +609,11 @@ k_pass(Work w, KeySpec ks, int L) {
         uint4* dst = w.tup[sg.buf ^ 1];
         const int d = sg.digit;
 
-        // Load: warp `warp` owns items [warp*512, warp*512+512), item k of a
-        // lane at warp*512 + k*32 + lane (coalesced, and k-major order is the
-        // input order, which keeps the ranks stable).
-        // rd[k] = (rank of item k among the warp's items of its digit) << 16
-        //        | digit (256 = no item).
+        // Warp `warp` owns items [warp*256, warp*256+256); item k of a lane
+        // is at warp*256 + k*32 + lane, so the k-major order is input order
+        // and the ranks below are stable.
         uint4 v[kPassItems];
-        uint32_t rd[kPassItems];
+        uint32_t rd[kPassItems];  // (rank among the warp's items of the digit) << 8 | digit
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
             uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
@@ -498,91 +621,94 @@ k_pass(Work w, KeySpec ks, int L) {
         }
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
-            uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
-            const uint32_t dk = idx < m ? digit_of(v[k], d) : 256u;
-            uint32_t peers = __match_any_sync(0xffffffffu, dk);
-            uint32_t cnt = dk < 256u ? wcnt[warp][dk] : 0u;
-            rd[k] = ((cnt + __popc(peers & lt_mask)) << 16) | dk;
-            __syncwarp();
-            if (dk < 256u && lane == __ffs(peers) - 1)
-                wcnt[warp][dk] = (uint16_t)(cnt + __popc(peers));
-            __syncwarp();
+            const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
+            const bool valid = idx < m;
+            const uint32_t dk = valid ? digit_of(v[k], d) : 0u;
+            rd[k] = (warp_rank(wcnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
         }
         __syncthreads();
-
-        // Thread `tid` owns digit tid: exclusive offsets over warps, then the
-        // tile's count is published for the look-back of later tiles.
-        const int dig = tid;
-        uint32_t run = 0;
-#pragma unroll
-        for (int ww = 0; ww < kPassThreads / 32; ww++) {
-            uint32_t c = wcnt[ww][dig];
-            wcnt[ww][dig] = (uint16_t)run;
-            run += c;
-        }
-        const uint32_t tile_cnt = run;
-        ull* my = w.status + (ull)t * kRadix + dig;
+        LEY_PHASE(2);
+        uint32_t tile_cnt = 0, incl = 0;
         ull excl = 0;
-        if (lt == 0) {
-            st_relaxed(my, pack_status(kFlagInc, epoch, tile_cnt));
-        } else {
-            st_relaxed(my, pack_status(kFlagAgg, epoch, tile_cnt));
-            // Decoupled look-back (Merrill & Garland): walk predecessors of
-            // this bucket, summing aggregates until an inclusive prefix.
-            uint32_t j = t - 1;
-            uint32_t spins = 0;
-            while (true) {
-                ull s = ld_relaxed(w.status + (ull)j * kRadix + dig);
-                int ep = (int)((s >> 56) & 0x3F);
-                ull flag = s & (3ull << 62);
-                if (ep != epoch || flag == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(w.err, kErrTimeout);
-                        sh_bad = 1;
-                        break;
-                    }
-                    if (spins > 32) __nanosleep(64);
-                    continue;
-                }
-                excl += s & kValMask;
-                if (flag == kFlagInc || j == tile0) break;
-                j--;
+        if (tid < kRadix) {
+            // Thread `tid` owns digit tid: exclusive offsets over warps, then
+            // the tile's count is published for the look-back of later tiles.
+            const int dig = tid;
+#pragma unroll
+            for (int ww = 0; ww < kPassWarps; ww++) {
+                uint32_t c = wcnt[ww][dig];
+                wcnt[ww][dig] = tile_cnt;
+                tile_cnt += c;
             }
-            st_relaxed(my, pack_status(kFlagInc, epoch, excl + tile_cnt));
-        }
-        // Block exclusive scan of the tile's digit counts: local offsets.
-        uint32_t incl = tile_cnt;
+            ull* my = w.status + (ull)t * kRadix + dig;
+            if (lt == 0) {
+                st_relaxed(my, pack_status(kFlagInc, epoch, tile_cnt));
+            } else {
+                st_relaxed(my, pack_status(kFlagAgg, epoch, tile_cnt));
+                // Decoupled look-back (Merrill & Garland): walk predecessors
+                // of this bucket, summing aggregates until an inclusive prefix.
+                uint32_t j = t - 1;
+                uint32_t spins = 0;
+                while (true) {
+                    ull s = ld_relaxed(w.status + (ull)j * kRadix + dig);
+                    int ep = (int)((s >> 56) & 0x3F);
+                    ull flag = s & (3ull << 62);
+                    if (ep != epoch || flag == 0) {
+                        if (++spins > kSpinLimit) {
+                            atomicOr(w.err, kErrTimeout);
+                            sh_bad = 1;
+                            break;
+                        }
+                        if (spins > 32) __nanosleep(64);
+                        continue;
+                    }
+                    excl += s & kValMask;
+                    if (flag == kFlagInc || j == tile0) break;
+                    j--;
+                }
+                st_relaxed(my, pack_status(kFlagInc, epoch, excl + tile_cnt));
+            }
+            // Exclusive scan of the tile's digit counts: local offsets.
+            incl = tile_cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) scan_tot[warp] = incl;
         }
-        if (lane == 31) warp_tot[warp] = incl;
         __syncthreads();
-        uint32_t wp = 0;
+        LEY_PHASE(3);
+        if (tid < kRadix) {
+            uint32_t wp = 0;
 #pragma unroll
-        for (int ww = 0; ww < kPassThreads / 32; ww++) wp += ww < warp ? warp_tot[ww] : 0u;
-        loc_off[dig] = wp + incl - tile_cnt;
-        gbase[dig] = sg.start + w.bucket_base[(ull)e * kRadix + dig] + excl;
+            for (int ww = 0; ww < kRadix / 32; ww++) wp += ww < warp ? scan_tot[ww] : 0u;
+            loc_off[tid] = wp + incl - tile_cnt;
+            gbase[tid] = sg.start + w.bucket_base[(ull)e * kRadix + tid] + excl;
+        }
         __syncthreads();
+        LEY_PHASE(4);
 
         // Stage the tile in shared memory in sorted-by-digit order.
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
-            const uint32_t dk = rd[k] & 0xFFFFu;
-            if (dk < 256u) stage[loc_off[dk] + wcnt[warp][dk] + (rd[k] >> 16)] = v[k];
+            const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
+            const uint32_t dk = rd[k] & 0xFFu;
+            if (idx < m) stage[loc_off[dk] + wcnt[warp][dk] + (rd[k] >> 8)] = v[k];
         }
         __syncthreads();
+        LEY_PHASE(5);
         if (sh_bad) continue;
         // Write each digit's run contiguously to its bucket.
         const ull seg_end = sg.start + sg.count;
         for (uint32_t i = tid; i < m; i += kPassThreads) {
-            uint4 tv = stage[i];
-            uint32_t dd = digit_of(tv, d);
-            ull pos = gbase[dd] + (i - loc_off[dd]);
+            const uint4 tv = stage[i];
+            const uint32_t dd = digit_of(tv, d);
+            const ull pos = gbase[dd] + (i - loc_off[dd]);
             if (pos >= sg.start && pos < seg_end) dst[pos] = tv;
             else atomicOr(w.err, kErrCapacity);
         }
+        LEY_PHASE(6);
     }
 }
 
@@ -606,37 +732,78 @@ struct Emitter<1> {  // pairs: sorted keys and their payloads
     }
 };
 
+// Shared state of one finishing CTA.  B holds the task's tuples; order[j] is
+// the position in B of the tuple whose final place in the task is j.
 struct FinShared {
-    uint16_t wcnt[kFinThreads / 32][kRadix];
-    uint16_t sb_off[kRadix];
-    uint16_t sb_cnt[kRadix];
-    uint32_t stk_s[kFinStack];
-    uint32_t stk_c[kFinStack];
-    uint32_t warp_tot[kFinThreads / 32];
+    uint32_t cnt[kFinWarps][kRadix];   // per-warp digit counters
+    uint16_t off[kFinWarps][kRadix];   // per-warp sub-bucket offsets (warp sorts)
+    uint16_t sb_off[kRadix];           // block counting pass: sub-bucket offsets
+    uint16_t sb_cnt[kRadix];           //   and sizes
+    uint16_t order[kSmall];
+    uint32_t q_meta[kFinQueue];        // warp queue: start | count << 16
+    uint8_t q_dig[kFinQueue];
+    uint8_t q_ready[kFinQueue];
+    uint32_t bs_meta[kFinStack];       // block stack (sub-buckets > kWarpMax)
+    uint8_t bs_dig[kFinStack];
+    int q_head, q_tail, q_pending, bs_n;
+    uint32_t warp_tot[kFinWarps];
     uint32_t d3[3];
-    int stk_n;
     uint32_t task;
 };
 
-// Sorts B[r0, r0+c) (or, when gsrc != nullptr, the c tuples at gsrc, staged
-// into B[0, c)) by key from digit d0 on.  Sub-buckets of at most kTiny tuples
-// are finished by comparison ranking; larger ones are pushed on the CTA's
-// stack.  Every finished tuple is emitted at out_base + its final position.
-template <int MODE>
-__device__ void fin_range(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0, uint32_t c,
-                          int d0, const KeySpec& ks, const Emitter<MODE>& emit, ull out_base,
-                          uint32_t* err) {
+// Rank of tuple tv among the c tuples at B[s..s+c) (strict (key, index) order).
+__device__ __forceinline__ uint32_t cmp_rank(const uint4* B, uint32_t s, uint32_t c,
+                                             const uint4& tv, uint32_t lo_mask) {
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < c; j++) r += tup_less(B[s + j], tv, lo_mask) ? 1u : 0u;
+    return r;
+}
+
+__device__ __forceinline__ void queue_push(FinShared& S, uint32_t s, uint32_t c, int d,
+                                           uint32_t* err) {
+    atomicAdd(&S.q_pending, 1);  // counted before it can be claimed
+    const int slot = atomicAdd(&S.q_tail, 1);
+    if (slot >= kFinQueue) {  // cannot happen (see kFinQueue); report and drop
+        atomicOr(err, kErrCapacity);
+        atomicSub(&S.q_pending, 1);
+        return;
+    }
+    S.q_meta[slot] = s | (c << 16);
+    S.q_dig[slot] = (uint8_t)d;
+    __threadfence_block();
+    S.q_ready[slot] = 1;
+    (void)err;
+}
+
+__device__ __forceinline__ void stack_push(FinShared& S, uint32_t s, uint32_t c, int d,
+                                           uint32_t* err) {
+    const int slot = atomicAdd(&S.bs_n, 1);
+    if (slot < kFinStack) {
+        S.bs_meta[slot] = s | (c << 16);
+        S.bs_dig[slot] = (uint8_t)d;
+    } else {
+        atomicOr(err, kErrCapacity);
+    }
+}
+
+// Sub-bucket of `c2` tuples at B[s2..): finished here by comparison ranking
+// when tiny, else queued for a warp (<= kWarpMax) or for the whole CTA.
+// Block-wide stable counting pass on B[r0, r0+c) -- or on the c tuples at
+// gsrc, staged into B[0, c) -- from digit d0 on (SingleThreadRadixSort of
+// Algorithm 1, one CTA instead of one thread).
+__device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0,
+                               uint32_t c, int d0, const KeySpec& ks, uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
     uint4 v[kFinItems];
-    uint32_t dg[kFinItems], rk[kFinItems];
+    uint32_t rd[kFinItems];
     if (tid < 3) S.d3[tid] = 0;
 #pragma unroll
-    for (int ww = 0; ww < kFinThreads / 32; ww++) S.wcnt[ww][tid] = 0;
+    for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
     const uint4 ref = gsrc ? gsrc[0] : B[r0];
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
-        uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
         v[k] = idx < c ? (gsrc ? gsrc[idx] : B[r0 + idx]) : ref;
     }
     ull dhi = 0;
@@ -646,7 +813,10 @@ __device__ void fin_range(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0
         dhi |= key_hi(v[k]) ^ key_hi(ref);
         dlo |= v[k].z ^ ref.z;
     }
-    __syncthreads();  // S.d3 / wcnt zeroed, all reads of B done
+    __syncthreads();  // counters zeroed, all reads of B done
+#ifdef LEY_PHASE_TIMING
+    if (gsrc && threadIdx.x == 0) atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
+#endif
     warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, S.d3);
     __syncthreads();
     const int ds = first_varying_digit(((ull)S.d3[0] << 32) | S.d3[1], S.d3[2], d0, ks.ndig);
@@ -654,93 +824,242 @@ __device__ void fin_range(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0
         // All keys equal: the input order is the answer.
 #pragma unroll
         for (int k = 0; k < kFinItems; k++) {
-            uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
-            if (idx < c) emit(out_base + r0 + idx, v[k]);
+            const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+            if (idx < c) {
+                if (gsrc) B[r0 + idx] = v[k];
+                S.order[r0 + idx] = (uint16_t)(r0 + idx);
+            }
         }
         return;
     }
-    // Stable counting pass on digit ds (ranks as in k_pass).
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
-        uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
-        dg[k] = idx < c ? digit_of(v[k], ds) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, dg[k]);
-        uint32_t cnt = dg[k] < 256u ? S.wcnt[warp][dg[k]] : 0u;
-        rk[k] = cnt + __popc(peers & lt_mask);
-        __syncwarp();
-        if (dg[k] < 256u && lane == __ffs(peers) - 1)
-            S.wcnt[warp][dg[k]] = (uint16_t)(cnt + __popc(peers));
-        __syncwarp();
+        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+        const bool valid = idx < c;
+        const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
+        rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
     }
     __syncthreads();
     {
         const int dig = tid;
         uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < kFinThreads / 32; ww++) {
-            uint32_t cc = S.wcnt[ww][dig];
-            S.wcnt[ww][dig] = (uint16_t)run;
+        for (int ww = 0; ww < kFinWarps; ww++) {
+            const uint32_t cc = S.cnt[ww][dig];
+            S.cnt[ww][dig] = run;
             run += cc;
         }
         uint32_t incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         if (lane == 31) S.warp_tot[warp] = incl;
         __syncthreads();
         uint32_t wp = 0;
 #pragma unroll
-        for (int ww = 0; ww < kFinThreads / 32; ww++) wp += ww < warp ? S.warp_tot[ww] : 0u;
+        for (int ww = 0; ww < kFinWarps; ww++) wp += ww < warp ? S.warp_tot[ww] : 0u;
         S.sb_off[dig] = (uint16_t)(wp + incl - run);
         S.sb_cnt[dig] = (uint16_t)run;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kFinItems; k++)
-        if (dg[k] < 256u) B[r0 + S.sb_off[dg[k]] + S.wcnt[warp][dg[k]] + rk[k]] = v[k];
+    for (int k = 0; k < kFinItems; k++) {
+        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+        const uint32_t dk = rd[k] & 0xFFu;
+        if (idx < c) B[r0 + S.sb_off[dk] + S.cnt[warp][dk] + (rd[k] >> 8)] = v[k];
+    }
     __syncthreads();
+    {
+        const uint32_t sc = S.sb_cnt[tid];
+        const uint32_t s2 = r0 + S.sb_off[tid];
+        if (sc > (uint32_t)kWarpMax) stack_push(S, s2, sc, ds + 1, err);
+        else if (sc > (uint32_t)kTiny) queue_push(S, s2, sc, ds + 1, err);
+    }
+#ifdef LEY_PHASE_TIMING
+    if (gsrc && threadIdx.x == 0) atomicAdd(&g_ley_phase[21], (unsigned long long)clock64());
+#endif
     // Tiny sub-buckets: rank by comparison (ComparisonSort of Algorithm 1).
     for (uint32_t i = tid; i < c; i += kFinThreads) {
         const uint4 tv = B[r0 + i];
         const uint32_t dd = digit_of(tv, ds);
-        const uint32_t so = S.sb_off[dd], sc = S.sb_cnt[dd];
+        const uint32_t sc = S.sb_cnt[dd];
         if (sc <= (uint32_t)kTiny) {
-            uint32_t r = 0;
-            for (uint32_t j = 0; j < sc; j++) r += tup_less(B[r0 + so + j], tv, ks.lo_mask) ? 1u : 0u;
-            emit(out_base + r0 + so + r, tv);
-        } else if (i == so) {
-            int slot = atomicAdd(&S.stk_n, 1);
-            if (slot < kFinStack) {
-                S.stk_s[slot] = r0 + so;
-                S.stk_c[slot] = sc;
-            } else {
-                atomicOr(err, kErrCapacity);
-            }
+            const uint32_t so = r0 + S.sb_off[dd];
+            S.order[so + cmp_rank(B, so, sc, tv, ks.lo_mask)] = (uint16_t)(r0 + i);
         }
     }
-    // caller synchronises before reading the stack
-    (void)ds;
+}
+
+// One warp sorts the c <= kWarpMax tuples at B[s, s+c) from digit d0 on:
+// a stable counting pass on the first digit where they differ, comparison
+// ranking of tiny sub-buckets, and larger ones back onto the queue.
+__device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, int d0,
+                              const KeySpec& ks, uint32_t* err) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt_mask = lanemask_lt();
+    uint32_t* cnt = S.cnt[warp];
+    uint16_t* off = S.off[warp];
+    const uint4 ref = B[s];
+    uint4 v[kFinItems];
+    uint32_t rd[kFinItems];
+    ull dhi = 0;
+    uint32_t dlo = 0;
+#pragma unroll
+    for (int k = 0; k < kFinItems; k++) {
+        const uint32_t idx = k * 32 + lane;
+        v[k] = idx < c ? B[s + idx] : ref;
+        dhi |= key_hi(v[k]) ^ key_hi(ref);
+        dlo |= v[k].z ^ ref.z;
+    }
+    dhi &= ks.hi_mask;
+    dlo &= ks.lo_mask;
+    const uint32_t a = __reduce_or_sync(0xffffffffu, (uint32_t)(dhi >> 32));
+    const uint32_t b = __reduce_or_sync(0xffffffffu, (uint32_t)dhi);
+    const uint32_t z = __reduce_or_sync(0xffffffffu, dlo);
+    const int ds = first_varying_digit(((ull)a << 32) | b, z, d0, ks.ndig);
+    if (ds >= ks.ndig) {
+        for (uint32_t i = lane; i < c; i += 32) S.order[s + i] = (uint16_t)(s + i);
+        __syncwarp();
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < kRadix / 32; k++) cnt[k * 32 + lane] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kFinItems; k++) {
+        const uint32_t idx = k * 32 + lane;
+        const bool valid = idx < c;
+        const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
+        rd[k] = (warp_rank(cnt, dk, valid, lt_mask, lane) << 8) | dk;
+    }
+    __syncwarp();
+    // Exclusive scan of the 256 counters: lane l owns bins 8l..8l+7.
+    uint32_t c8[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        c8[k] = cnt[lane * 8 + k];
+        sum += c8[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        off[lane * 8 + k] = (uint16_t)run;
+        run += c8[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kFinItems; k++) {
+        const uint32_t idx = k * 32 + lane;
+        const uint32_t dk = rd[k] & 0xFFu;
+        if (idx < c) B[s + off[dk] + (rd[k] >> 8)] = v[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        if (c8[k] > (uint32_t)kTiny) queue_push(S, s + off[lane * 8 + k], c8[k], ds + 1, err);
+    for (uint32_t i = lane; i < c; i += 32) {
+        const uint4 tv = B[s + i];
+        const uint32_t dd = digit_of(tv, ds);
+        const uint32_t sc = cnt[dd];
+        if (sc <= (uint32_t)kTiny) {
+            const uint32_t so = s + off[dd];
+            S.order[so + cmp_rank(B, so, sc, tv, ks.lo_mask)] = (uint16_t)(s + i);
+        }
+    }
+    __syncwarp();
+}
+
+// Warps take queued sub-buckets until every queued one is finished
+// (the small-bucket queue of Algorithm 1, drained by the CTA's warps).
+__device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t idle = 0;
+    while (true) {
+        // Lane 0 claims an entry and reads it; the warp acts on the broadcast.
+        int slot = -1, pending = 0;
+        uint32_t meta = 0, dg = 0, ok = 1;
+        if (lane == 0) {
+            const int h = *(volatile int*)&S.q_head;
+            const int tl = min(*(volatile int*)&S.q_tail, kFinQueue);
+            if (h < tl && atomicCAS(&S.q_head, h, h + 1) == h) {
+                slot = h;
+                uint32_t spins = 0;
+                while (*(volatile uint8_t*)&S.q_ready[slot] == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(err, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __threadfence_block();
+                meta = *(volatile uint32_t*)&S.q_meta[slot];
+                dg = *(volatile uint8_t*)&S.q_dig[slot];
+                *(volatile uint8_t*)&S.q_ready[slot] = 0;
+            } else {
+                pending = *(volatile int*)&S.q_pending;
+            }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= 0) {
+            meta = __shfl_sync(0xffffffffu, meta, 0);
+            dg = __shfl_sync(0xffffffffu, dg, 0);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            const uint32_t s0 = meta & 0xFFFFu, c0 = meta >> 16;
+            if (ok && s0 + c0 <= (uint32_t)kSmall && c0 <= (uint32_t)kWarpMax)
+                fin_warp_sort(B, S, s0, c0, (int)dg, ks, err);
+            else if (lane == 0)
+                atomicOr(err, kErrCapacity);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicSub(&S.q_pending, 1);
+            }
+            idle = 0;
+        } else {
+            pending = __shfl_sync(0xffffffffu, pending, 0);
+            if (pending == 0) break;
+            if (++idle > kSpinLimit) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kFinThreads)
+__global__ void __launch_bounds__(kFinThreads, 4)
 k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     extern __shared__ uint4 B[];  // kSmall tuples
     __shared__ FinShared S;
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
+    for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
+    LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
+        LEY_PHASE(10);
         if (tid == 0) {
             S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
-            S.stk_n = 0;
+            S.q_head = S.q_tail = S.q_pending = S.bs_n = 0;
         }
         __syncthreads();
         const uint32_t ti = S.task;
         if (ti >= nfin) break;
+        LEY_PHASE(11);
         const FinTask tk = w.fin[ti];
+        if (tk.start + tk.count > w.n || tk.buf > 1) {  // never for a valid task list
+            if (tid == 0) atomicOr(w.err, kErrCapacity);
+            continue;
+        }
         const uint4* src = w.tup[tk.buf] + tk.start;
         if (tk.flags & 1) {  // all keys equal: input order
             for (uint32_t i = tid; i < tk.count; i += kFinThreads) emit(tk.start + i, src[i]);
@@ -750,19 +1069,37 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             if (tid == 0) atomicOr(w.err, kErrCapacity);
             continue;
         }
-        fin_range<MODE>(B, S, src, 0, tk.count, tk.digit, ks, emit, tk.start, w.err);
+        fin_block_pass(B, S, src, 0, tk.count, tk.digit, ks, w.err);
+        __syncthreads();
+        LEY_PHASE(12);
         while (true) {
             __syncthreads();
-            const int ns = S.stk_n;
+            fin_drain_queue(B, S, ks, w.err);
+            __syncthreads();
+            const int ns = S.bs_n;
             if (ns <= 0) break;
             const int top = (ns > kFinStack ? kFinStack : ns) - 1;
-            const uint32_t s0 = S.stk_s[top], c0 = S.stk_c[top];
+            const uint32_t meta = S.bs_meta[top];
+            const int dg = S.bs_dig[top];
             __syncthreads();
-            if (tid == 0) S.stk_n = top;
-            // digit: the sub-bucket's first digit is shared, so restarting at
-            // 0 only costs the difference scan; keys decide.
-            fin_range<MODE>(B, S, nullptr, s0, c0, 0, ks, emit, tk.start, w.err);
+            if (tid == 0) S.bs_n = top;
+            if ((meta & 0xFFFFu) + (meta >> 16) > (uint32_t)kSmall) {
+                if (tid == 0) atomicOr(w.err, kErrCapacity);
+                continue;
+            }
+            fin_block_pass(B, S, nullptr, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
         }
+        LEY_PHASE(13);
+        // Coalesced write of the task's final order.
+        for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
+            uint32_t o = S.order[j];
+            if (o >= tk.count) {  // a position left unset: report, stay in bounds
+                atomicOr(w.err, kErrCapacity);
+                o = 0;
+            }
+            emit(tk.start + j, B[o]);
+        }
+        LEY_PHASE(14);
     }
 }
 
@@ -776,6 +1113,16 @@ __global__ void k_partition_out(Work w, ull n, uint32_t* order_out, ull* hist_ou
 }
 
 // -------------------------------------------------------------- launchers
+#ifdef LEY_PHASE_TIMING
+}  // namespace ley
+extern "C" int ley_phase_read(unsigned long long* out) {
+    cudaMemcpyFromSymbol(out, ley::g_ley_phase, sizeof(unsigned long long) * 64);
+    static unsigned long long zero[64];
+    cudaMemcpyToSymbol(ley::g_ley_phase, zero, sizeof(zero));
+    return 0;
+}
+namespace ley {
+#endif
 
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, ull n, uint32_t rec,
                                    KeySpec ks, const Work& w, int hist_digit) {
@@ -800,7 +1147,7 @@ cudaError_t launch_init(cudaStream_t s, const Work& w, ull n, int digit0) {
 }
 
 cudaError_t launch_hist(const LaunchCfg& c, const Work& w, KeySpec ks, int level) {
-    k_hist<<<c.grid, kPassThreads, 0, c.stream>>>(w, ks, level);
+    k_hist<<<c.grid, kHistThreads, 0, c.stream>>>(w, ks, level);
     return cudaGetLastError();
 }
 
@@ -810,7 +1157,7 @@ cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int l
 }
 
 cudaError_t launch_classify_partition(cudaStream_t s, const Work& w) {
-    k_classify_partition<<<1, 32, 0, s>>>(w);
+    k_classify_partition<<<64, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -856,8 +1203,8 @@ size_t kernel_smem(KernelKind k) {
 
 int kernel_threads(KernelKind k) {
     switch (k) {
-        case KK_PASS:
-        case KK_HIST: return kPassThreads;
+        case KK_PASS: return kPassThreads;
+        case KK_HIST: return kHistThreads;
         case KK_FINISH_REC:
         case KK_FINISH_PAIRS: return kFinThreads;
         default: return 256;
@@ -879,7 +1226,7 @@ int blocks_per_sm(KernelKind k) {
         g_bps[KK_EXTRACT_REC] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_extract_pairs, 256, 0);
         g_bps[KK_EXTRACT_PAIRS] = v > 0 ? v : 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_hist, kPassThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_hist, kHistThreads, 0);
         g_bps[KK_HIST] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pass, kPassThreads,
                                                       kernel_smem(KK_PASS));

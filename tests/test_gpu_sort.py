@@ -113,8 +113,8 @@ def test_other_geometries_exact(orc, ley, rec_bytes, key_bytes):
     check_exact(orc, ley, rec, key_bytes=key_bytes)
 
 
-def test_tma_gather_variant_exact(orc, ley, monkeypatch):
-    monkeypatch.setenv("LEY_GATHER", "tma")
+def test_lsu_gather_variant_exact(orc, ley, monkeypatch):
+    monkeypatch.setenv("LEY_GATHER", "lsu")
     for n in [1, 31, 33, 4096, 100_003]:
         check_exact(orc, ley, datagen.uniform_records(n, seed=n + 5))
 
