@@ -39,11 +39,14 @@ class _KernelTime(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this binding loads: the in-tree build, or the file named by
+    the LEYSORT_LIB environment variable (an alternative build of the same
+    sources, e.g. one with kernel phase timers)."""
+    return os.environ.get("LEYSORT_LIB") or _build.LIB
 
 
 def _load() -> ctypes.CDLL:
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         raise ImportError(
             f"libleysort.so is not built ({path}); run "

@@ -1,6 +1,7 @@
 // C ABI of leysort: argument checks, scratch layout, the launch sequence of
 // the internal sort, and the host-memory (partially in-memory) mode.
 #include <atomic>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -88,6 +89,14 @@ static cudaError_t launch(const char* name, cudaStream_t s, F&& f) {
     if (on) cudaEventRecord(a, s);
     cudaError_t e = f();
     g_launches.fetch_add(1);
+    // LEY_DEBUG_SYNC=1: wait for every kernel and name the first that fails
+    // (a debugging aid; off by default).
+    static const bool dbg_sync = std::getenv("LEY_DEBUG_SYNC") != nullptr;
+    if (dbg_sync && e == cudaSuccess) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            std::fprintf(stderr, "leysort: kernel %s failed: %s\n", name, cudaGetErrorString(e));
+    }
     if (on) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         cudaEvent_t b = take_event();
@@ -100,10 +109,10 @@ static cudaError_t launch(const char* name, cudaStream_t s, F&& f) {
 // ---------------------------------------------------------------- layout
 
 struct Layout {
-    size_t tup[2], perm, ctl, segs[2], stb[2], sto[2], hist[2], diff[2], pslot, ptb, pto, bb, fin,
+    size_t tup[2], perm, ctl, segs[2], stb[2], sto[2], spass[2], hist[2], diff[2], tcnt, bb, fin,
         status;
     size_t total;
-    ull cap_seg, cap_fin, cap_tiles;
+    ull cap_seg, cap_fin, cap_tiles, cap_chunks;
 };
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -112,6 +121,7 @@ static Layout make_layout(ull n, bool with_perm) {
     Layout L{};
     L.cap_seg = n / kSmall + 2;
     L.cap_tiles = n / kPassTile + L.cap_seg + 1;
+    L.cap_chunks = L.cap_tiles / kScanChunk + 1;
     L.cap_fin = 100 * (n / kSmall + 1) + 16;
     size_t off = 0;
     auto put = [&](size_t bytes) {
@@ -127,15 +137,14 @@ static Layout make_layout(ull n, bool with_perm) {
         L.segs[p] = put(L.cap_seg * sizeof(Seg));
         L.stb[p] = put(L.cap_seg * sizeof(uint32_t));
         L.sto[p] = put(L.cap_tiles * sizeof(uint32_t));
+        L.spass[p] = put(L.cap_seg * sizeof(uint32_t));
         L.hist[p] = put(L.cap_seg * kRadix * sizeof(uint32_t));
         L.diff[p] = put(L.cap_seg * sizeof(Diff));
     }
-    L.pslot = put(L.cap_seg * sizeof(uint32_t));
-    L.ptb = put(L.cap_seg * sizeof(uint32_t));
-    L.pto = put(L.cap_tiles * sizeof(uint32_t));
+    L.tcnt = put(L.cap_tiles * kRadix * sizeof(uint32_t));
     L.bb = put(L.cap_seg * kRadix * sizeof(uint32_t));
     L.fin = put(L.cap_fin * sizeof(FinTask));
-    L.status = put(L.cap_tiles * kRadix * sizeof(ull));
+    L.status = put(L.cap_chunks * kRadix * sizeof(ull));
     L.total = off;
     return L;
 }
@@ -150,12 +159,11 @@ static Work make_work(char* base, const Layout& L, ull n, uint32_t* err) {
         w.segs[p] = reinterpret_cast<Seg*>(base + L.segs[p]);
         w.seg_tile_base[p] = reinterpret_cast<uint32_t*>(base + L.stb[p]);
         w.seg_tile_owner[p] = reinterpret_cast<uint32_t*>(base + L.sto[p]);
+        w.seg_pass[p] = reinterpret_cast<uint32_t*>(base + L.spass[p]);
         w.hist[p] = reinterpret_cast<uint32_t*>(base + L.hist[p]);
         w.diff[p] = reinterpret_cast<Diff*>(base + L.diff[p]);
     }
-    w.pass_slot = reinterpret_cast<uint32_t*>(base + L.pslot);
-    w.pass_tile_base = reinterpret_cast<uint32_t*>(base + L.ptb);
-    w.pass_tile_owner = reinterpret_cast<uint32_t*>(base + L.pto);
+    w.tile_cnt = reinterpret_cast<uint32_t*>(base + L.tcnt);
     w.bucket_base = reinterpret_cast<uint32_t*>(base + L.bb);
     w.fin = reinterpret_cast<FinTask*>(base + L.fin);
     w.status = reinterpret_cast<ull*>(base + L.status);
@@ -163,6 +171,7 @@ static Work make_work(char* base, const Layout& L, ull n, uint32_t* err) {
     w.cap_seg = L.cap_seg;
     w.cap_fin = L.cap_fin;
     w.cap_tiles = L.cap_tiles;
+    w.cap_chunks = L.cap_chunks;
     w.n = n;
     return w;
 }
@@ -221,9 +230,8 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
     const KeySpec ks = a.mode == MODE_PAIRS ? pair_keyspec() : record_keyspec(a.kb);
     const int sms = ds->sms;
     LEY_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
-    LEY_TRY(cudaMemsetAsync(w.hist[0], 0, kRadix * sizeof(uint32_t), st));
     LEY_TRY(cudaMemsetAsync(w.diff[0], 0, sizeof(Diff), st));
-    LEY_TRY(cudaMemsetAsync(w.status, 0, L.cap_tiles * kRadix * sizeof(ull), st));
+    LEY_TRY(cudaMemsetAsync(w.status, 0, L.cap_chunks * kRadix * sizeof(ull), st));
     const int digit0 = a.mode == MODE_PARTITION ? (int)a.digit : 0;
     LEY_TRY(launch("init", st, [&] { return launch_init(st, w, a.n, digit0); }));
     if (a.mode == MODE_PAIRS) {
@@ -238,7 +246,9 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
         }));
     }
     const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
+    const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     if (a.mode == MODE_PARTITION) {
+        LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, 0); }));
         LEY_TRY(launch("classify", st, [&] { return launch_classify_partition(st, w); }));
         LEY_TRY(launch("pass", st, [&] { return launch_pass(cp, w, ks, 0); }));
         LEY_TRY(launch("partition_out", st, [&] {
@@ -250,6 +260,7 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
     const LaunchCfg cc{2 * sms, 128, 0, st};
     for (int lvl = 0; lvl < ks.ndig; lvl++) {
         if (lvl > 0) LEY_TRY(launch("hist", st, [&] { return launch_hist(ch, w, ks, lvl); }));
+        LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, lvl); }));
         LEY_TRY(launch("classify", st, [&] { return launch_classify(cc, w, ks, lvl); }));
         LEY_TRY(launch("pass", st, [&] { return launch_pass(cp, w, ks, lvl); }));
     }
@@ -463,9 +474,13 @@ ley_status ley_last_device_status(ley_stream_t stream) {
     if (!ds) return LEY_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return LEY_ECUDA;
-    uint32_t v = 0;
-    if (cudaMemcpy(&v, ds->err, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return LEY_ECUDA;
-    if (v && cudaMemset(ds->err, 0, sizeof(v)) != cudaSuccess) return LEY_ECUDA;
+    uint32_t ev[2] = {0, 0};
+    if (cudaMemcpy(ev, ds->err, sizeof(ev), cudaMemcpyDeviceToHost) != cudaSuccess) return LEY_ECUDA;
+    const uint32_t v = ev[0];
+    if (v && cudaMemset(ds->err, 0, sizeof(ev)) != cudaSuccess) return LEY_ECUDA;
+    if (v && std::getenv("LEY_DEBUG"))
+        std::fprintf(stderr, "leysort: device error bits 0x%x first raised at file %u line %u\n", v,
+                     ev[1] >> 16, ev[1] & 0xFFFFu);
     if (v & kErrTimeout) return LEY_ETIMEOUT;
     if (v & kErrCapacity) return LEY_ENOMEM;
     return LEY_OK;

@@ -9,6 +9,7 @@
 // contiguous output bytes per warp in shared memory, then write the tile with
 // 16-byte stores (LSU kernel) or one TMA bulk store (TMA kernel).  No access
 // leaves a 16-byte granule that holds record bytes.
+#define LEY_FILE_ID 2
 #include "ley_kernels.h"
 
 namespace ley {
@@ -71,7 +72,7 @@ k_gather100(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
         if (valid) {
             uint32_t pj = __ldg(perm + j);
             if (pj >= n) {  // never for a valid permutation; keeps reads in bounds
-                atomicOr(err, kErrCapacity);
+                LEY_FAIL(err, kErrCapacity);
                 pj = 0;
             }
             const ull s = (ull)pj * kRec;
@@ -256,7 +257,7 @@ k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
         if (cn < nchunks) o[b] = tma_issue(wb, &bars[warp][b], b, cn, in, perm, n, lane);
     }
     if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
+        if (lane == 0) LEY_FAIL(err, kErrTimeout);
         // Give copies still in flight a bounded chance to land before exit.
         for (int b = 0; b < kTmaBufs; b++) (void)mbar_wait(&bars[warp][b], phase[b]);
     }

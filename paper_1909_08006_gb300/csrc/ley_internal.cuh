@@ -28,6 +28,9 @@ constexpr int kPassItems = kPassTile / kPassThreads;   // 8
 constexpr int kPassWarps = kPassThreads / 32;          // 16
 constexpr int kHistThreads = 256;
 constexpr int kHistItems = kPassTile / kHistThreads;   // 16
+// Tiles per chunk of the per-tile offset scan.
+constexpr int kScanChunk = 16;
+constexpr uint32_t kNoPass = 0xFFFFFFFFu;
 
 // In-CTA finishing (the small-bucket queue of Algorithm 1): 256 threads x 8.
 constexpr int kFinThreads = 256;
@@ -45,6 +48,17 @@ constexpr int kFinStack = kSmall / (kWarpMax + 1) + 2;       // block stack (> k
 // Device-side error bits (latched in the per-device status word).
 constexpr uint32_t kErrTimeout = 1u;
 constexpr uint32_t kErrCapacity = 2u;
+
+// Latches an error bit in the per-device status word and, for the first
+// error only, where it was raised: (source file id << 16) | line.
+__device__ __forceinline__ void ley_fail(uint32_t* err, uint32_t code, uint32_t site) {
+    atomicOr(err, code);
+    atomicCAS(err + 1, 0u, site);
+}
+#ifndef LEY_FILE_ID
+#define LEY_FILE_ID 0
+#endif
+#define LEY_FAIL(err, code) ::ley::ley_fail((err), (code), (LEY_FILE_ID << 16) | __LINE__)
 
 // Bounded waits: polls before a wait gives up (with nanosleep backoff this is
 // well under a second on a healthy GPU, and terminates on a broken one).
@@ -78,10 +92,9 @@ struct __align__(16) Diff {
 
 struct LevelCtl {
     unsigned long long big_packed;   // (#segments << 40) | #tiles of list L
-    unsigned long long pass_packed;  // (#pass entries << 40) | #tiles of pass L
-    uint32_t hist_tile_ctr;
-    uint32_t pass_tile_ctr;
-    uint32_t pad[2];
+    unsigned long long pass_count;   // buckets scattered at level L
+    uint32_t scan_chunk_ctr;
+    uint32_t pad[3];
 };
 
 struct Ctl {
@@ -109,17 +122,16 @@ struct Work {
     Ctl* ctl;
     Seg* segs[2];                 // big list per level parity
     uint32_t* seg_tile_base[2];
-    uint32_t* hist[2];            // [cap_seg][256]
-    Diff* diff[2];
     uint32_t* seg_tile_owner[2];  // tile -> slot in the big list
-    uint32_t* pass_slot;          // pass entry -> slot in list
-    uint32_t* pass_tile_base;
-    uint32_t* pass_tile_owner;    // pass tile -> pass entry
+    uint32_t* seg_pass[2];        // slot -> bucket_base row, or kNoPass
+    uint32_t* hist[2];            // [cap_seg][256] bucket sizes
+    Diff* diff[2];
+    uint32_t* tile_cnt;           // [cap_tiles][256] digit counts, then offsets
     uint32_t* bucket_base;        // [cap_seg][256] exclusive offsets
     FinTask* fin;
-    unsigned long long* status;   // [cap_tiles][256] look-back words
+    unsigned long long* status;   // [cap_chunks][256] scan look-back words
     uint32_t* err;                // per-device status word
-    unsigned long long cap_seg, cap_fin, cap_tiles;
+    unsigned long long cap_seg, cap_fin, cap_tiles, cap_chunks;
     unsigned long long n;
 };
 

@@ -20,6 +20,7 @@ cudaError_t launch_extract_pairs(const LaunchCfg& c, const uint64_t* keys, const
                                  unsigned long long n, KeySpec ks, const Work& w);
 cudaError_t launch_init(cudaStream_t s, const Work& w, unsigned long long n, int digit0);
 cudaError_t launch_hist(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
+cudaError_t launch_scan(const LaunchCfg& c, const Work& w, int level);
 cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
 cudaError_t launch_classify_partition(cudaStream_t s, const Work& w);
 cudaError_t launch_pass(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
@@ -34,7 +35,7 @@ cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsign
 
 // Occupancy-derived persistent grid sizes (blocks per SM) for a kernel kind.
 enum KernelKind {
-    KK_EXTRACT_REC = 0, KK_EXTRACT_PAIRS, KK_HIST, KK_PASS, KK_FINISH_REC, KK_FINISH_PAIRS,
+    KK_EXTRACT_REC = 0, KK_EXTRACT_PAIRS, KK_HIST, KK_SCAN, KK_PASS, KK_FINISH_REC, KK_FINISH_PAIRS,
     KK_GATHER100, KK_GATHER100_TMA, KK_GATHER_GENERIC, KK_COUNT
 };
 int blocks_per_sm(KernelKind k);

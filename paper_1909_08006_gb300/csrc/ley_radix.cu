@@ -18,6 +18,7 @@
 //                 memory by MSD counting passes, with comparison ranking for
 //                 tiny sub-buckets (SingleThreadRadixSort / ComparisonSort of
 //                 Algorithm 1), and emits the final permutation.
+#define LEY_FILE_ID 1
 #include "ley_kernels.h"
 
 namespace ley {
@@ -154,7 +155,8 @@ __device__ __forceinline__ uint32_t peers8(uint32_t dg) {
 // Stable rank of this lane's item among the warp's items with the same digit
 // so far: counter value before this step (returned by the group leader's
 // shared-memory atomic, broadcast by shuffle) plus the lower lanes of the
-// group.  Successive calls of a warp see its counters in program order.
+// group.  The leaders of successive calls are different lanes, so the
+// __syncwarp orders each call's atomics before the next call's.
 __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool valid,
                                               uint32_t lt_mask, int lane) {
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
@@ -162,94 +164,113 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool v
     const int leader = valid ? __ffs(peers) - 1 : lane;
     uint32_t old = 0;
     if (valid && lane == leader) old = atomicAdd(&cnt[dg], (uint32_t)__popc(peers));
+    __syncwarp();
     old = __shfl_sync(0xffffffffu, old, leader);
     return old + __popc(peers & lt_mask);
 }
 
 // ------------------------------------------------------------- extract
 
+// One tile = kPassTile consecutive records: its digit counts go to
+// tile_cnt[t] (the per-tile histogram of Section 3.1's "compute a histogram
+// based on the current radix"), its tuples to tup in input order.
 template <int REC>
 __global__ void __launch_bounds__(256)
-k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpec ks,
-                  uint4* __restrict__ tup, uint32_t* __restrict__ hist0, Diff* __restrict__ diff0,
+k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpec ks, Work w,
                   int hist_digit) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
-    sh_hist[threadIdx.x] = 0;
     if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t kb = (uint32_t)ks.ndig;
     const uint4 ref = load_record_key<REC>(in, 0, rec_rt, kb, ks);
+    uint4* __restrict__ tup = w.tup[0];
     ull dhi = 0;
     uint32_t dlo = 0;
     constexpr int U = 4;
-    const ull stride = (ull)gridDim.x * blockDim.x;
-    for (ull base = (ull)blockIdx.x * blockDim.x; base < n; base += stride * U) {
-        uint4 t[U];
-        bool valid[U];
+    const uint32_t ntiles = ceil_div_u64(n, kPassTile);
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();
+        sh_hist[threadIdx.x] = 0;
+        __syncthreads();
+        const ull base = (ull)t * kPassTile;
+#pragma unroll 1
+        for (int k0 = 0; k0 < kPassTile / 256; k0 += U) {
+            uint4 tv[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            ull i = base + u * stride + threadIdx.x;
-            valid[u] = i < n;
-            t[u] = valid[u] ? load_record_key<REC>(in, i, rec_rt, kb, ks) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            ull i = base + u * stride + threadIdx.x;
-            uint32_t dg = 256u;
-            if (valid[u]) {
-                t[u].w = (uint32_t)i;
-                tup[i] = t[u];
-                dg = digit_of(t[u], hist_digit);
-                dhi |= key_hi(t[u]) ^ key_hi(ref);
-                dlo |= t[u].z ^ ref.z;
+            for (int u = 0; u < U; u++) {
+                const ull i = base + (k0 + u) * 256 + threadIdx.x;
+                tv[u] = i < n ? load_record_key<REC>(in, i, rec_rt, kb, ks) : ref;
             }
-            hist_add_vote(sh_hist, dg);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = base + (k0 + u) * 256 + threadIdx.x;
+                uint32_t dg = 256u;
+                if (i < n) {
+                    tv[u].w = (uint32_t)i;
+                    tup[i] = tv[u];
+                    dg = digit_of(tv[u], hist_digit);
+                    dhi |= key_hi(tv[u]) ^ key_hi(ref);
+                    dlo |= tv[u].z ^ ref.z;
+                }
+                hist_add_vote(sh_hist, dg);
+            }
         }
+        __syncthreads();
+        w.tile_cnt[(ull)t * kRadix + threadIdx.x] = sh_hist[threadIdx.x];
+        if (threadIdx.x == 0) w.seg_tile_owner[0][t] = 0;
     }
     warp_or_diff(dhi, dlo, sh_d);
     __syncthreads();
-    if (sh_hist[threadIdx.x]) atomicAdd(&hist0[threadIdx.x], sh_hist[threadIdx.x]);
-    if (threadIdx.x == 0) flush_diff(sh_d, diff0);
+    if (threadIdx.x == 0) flush_diff(sh_d, w.diff[0]);
 }
 
 __global__ void __launch_bounds__(256)
 k_extract_pairs(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ idx, ull n,
-                uint4* __restrict__ tup, uint32_t* __restrict__ hist0, Diff* __restrict__ diff0) {
+                Work w) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
-    sh_hist[threadIdx.x] = 0;
     if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
     __syncthreads();
     const ull ref = __ldg(keys);
+    uint4* __restrict__ tup = w.tup[0];
     ull dhi = 0;
-    constexpr int U = 4;
-    const ull stride = (ull)gridDim.x * blockDim.x;
-    for (ull base = (ull)blockIdx.x * blockDim.x; base < n; base += stride * U) {
-        ull k[U];
-        uint32_t v[U];
+    constexpr int U = 8;
+    const uint32_t ntiles = ceil_div_u64(n, kPassTile);
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();
+        sh_hist[threadIdx.x] = 0;
+        __syncthreads();
+        const ull base = (ull)t * kPassTile;
+#pragma unroll 1
+        for (int k0 = 0; k0 < kPassTile / 256; k0 += U) {
+            ull kk[U];
+            uint32_t vv[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            ull i = base + u * stride + threadIdx.x;
-            k[u] = i < n ? __ldg(keys + i) : 0ull;
-            v[u] = i < n ? __ldg(idx + i) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            ull i = base + u * stride + threadIdx.x;
-            uint32_t dg = 256u;
-            if (i < n) {
-                tup[i] = make_uint4((uint32_t)k[u], (uint32_t)(k[u] >> 32), v[u], (uint32_t)i);
-                dg = (uint32_t)(k[u] >> 56);
-                dhi |= k[u] ^ ref;
+            for (int u = 0; u < U; u++) {
+                const ull i = base + (k0 + u) * 256 + threadIdx.x;
+                kk[u] = i < n ? __ldg(keys + i) : ref;
+                vv[u] = i < n ? __ldg(idx + i) : 0u;
             }
-            hist_add_vote(sh_hist, dg);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = base + (k0 + u) * 256 + threadIdx.x;
+                uint32_t dg = 256u;
+                if (i < n) {
+                    tup[i] = make_uint4((uint32_t)kk[u], (uint32_t)(kk[u] >> 32), vv[u], (uint32_t)i);
+                    dg = (uint32_t)(kk[u] >> 56);
+                    dhi |= kk[u] ^ ref;
+                }
+                hist_add_vote(sh_hist, dg);
+            }
         }
+        __syncthreads();
+        w.tile_cnt[(ull)t * kRadix + threadIdx.x] = sh_hist[threadIdx.x];
+        if (threadIdx.x == 0) w.seg_tile_owner[0][t] = 0;
     }
     warp_or_diff(dhi, 0u, sh_d);
     __syncthreads();
-    if (sh_hist[threadIdx.x]) atomicAdd(&hist0[threadIdx.x], sh_hist[threadIdx.x]);
-    if (threadIdx.x == 0) flush_diff(sh_d, diff0);
+    if (threadIdx.x == 0) flush_diff(sh_d, w.diff[0]);
 }
 
 __global__ void k_init(Work w, ull n, int digit0) {
@@ -268,32 +289,30 @@ __global__ void k_init(Work w, ull n, int digit0) {
 
 // ------------------------------------------------------------ histogram
 
+// Per-tile digit counts of every big bucket of level L >= 1 (the tiles of a
+// bucket are consecutive), and the bits in which each bucket's keys differ.
 __global__ void __launch_bounds__(kHistThreads)
 k_hist(Work w, KeySpec ks, int L) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
-    __shared__ uint32_t sh_tile;
     const int p = L & 1;
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
     const uint32_t ntiles = (uint32_t)(packed & kPackMask);
     const int tid = threadIdx.x;
     if (nseg > w.cap_seg || ntiles > w.cap_tiles) {  // an append overflowed
-        if (tid == 0 && blockIdx.x == 0) atomicOr(w.err, kErrCapacity);
+        if (tid == 0 && blockIdx.x == 0) LEY_FAIL(w.err, kErrCapacity);
         return;
     }
-    while (true) {
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        if (tid == 0) sh_tile = atomicAdd(&w.ctl->lvl[L].hist_tile_ctr, 1u);
         sh_hist[tid] = 0;
         if (tid < 3) sh_d[tid] = 0;
         __syncthreads();
-        const uint32_t t = sh_tile;
-        if (t >= ntiles) break;
         const uint32_t s = w.seg_tile_owner[p][t];
         const Seg sg = w.segs[p][s];
         if (s >= nseg || sg.start + sg.count > w.n || t < w.seg_tile_base[p][s] || sg.buf > 1) {
-            if (tid == 0) atomicOr(w.err, kErrCapacity);  // never for a valid list
+            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);  // never for a valid list
             continue;
         }
         const uint32_t lt = t - w.seg_tile_base[p][s];
@@ -318,8 +337,113 @@ k_hist(Work w, KeySpec ks, int L) {
         }
         warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, sh_d);
         __syncthreads();
-        if (sh_hist[tid]) atomicAdd(&w.hist[p][(ull)s * kRadix + tid], sh_hist[tid]);
+        w.tile_cnt[(ull)t * kRadix + tid] = sh_hist[tid];
         if (tid == 0) flush_diff(sh_d, &w.diff[p][s]);
+    }
+}
+
+// ----------------------------------------------------------------- scan
+
+constexpr ull kFlagAgg = 1ull << 62;
+constexpr ull kFlagInc = 2ull << 62;
+constexpr ull kValMask = (1ull << 56) - 1;
+
+__device__ __forceinline__ ull pack_status(ull flag, int epoch, ull val) {
+    return flag | ((ull)epoch << 56) | (val & kValMask);
+}
+
+// Turns the per-tile digit counts of level L into per-tile exclusive offsets
+// inside each bucket (in place), and writes each bucket's total per digit.
+// A single-pass segmented scan over chunks of kScanChunk tiles with
+// decoupled look-back (Merrill & Garland): a chunk that contains the first
+// tile of a bucket publishes its inclusive value at once; others publish
+// their aggregate and sum predecessors' values until an inclusive one.
+// Chunks are taken in order from a counter, so every predecessor of a chunk
+// is already running.
+__global__ void __launch_bounds__(kRadix)
+k_scan(Work w, int L) {
+    __shared__ uint32_t sh_own[kScanChunk];
+    __shared__ uint8_t sh_head[kScanChunk];
+    __shared__ uint8_t sh_last[kScanChunk];
+    __shared__ uint32_t sh_chunk;
+    const int p = L & 1;
+    const ull packed = w.ctl->lvl[L].big_packed;
+    const uint32_t nseg = (uint32_t)(packed >> kPackShift);
+    const uint32_t ntiles = (uint32_t)(packed & kPackMask);
+    const uint32_t nchunks = ceil_div_u64(ntiles, kScanChunk);
+    const int d = threadIdx.x;
+    const int epoch = L + 1;
+    if (nseg > w.cap_seg || ntiles > w.cap_tiles || nchunks > w.cap_chunks) {
+        if (d == 0 && blockIdx.x == 0) LEY_FAIL(w.err, kErrCapacity);
+        return;
+    }
+    while (true) {
+        __syncthreads();
+        if (d == 0) sh_chunk = atomicAdd(&w.ctl->lvl[L].scan_chunk_ctr, 1u);
+        __syncthreads();
+        const uint32_t k = sh_chunk;
+        if (k >= nchunks) break;
+        const uint32_t t0 = k * kScanChunk;
+        const uint32_t nt = min((uint32_t)kScanChunk, ntiles - t0);
+        if (d < (int)nt) {
+            const uint32_t t = t0 + d;
+            const uint32_t s = w.seg_tile_owner[p][t];
+            sh_own[d] = s;
+            sh_head[d] = s < nseg && w.seg_tile_base[p][s] == t;
+            sh_last[d] = t + 1 == ntiles || w.seg_tile_owner[p][t + 1] != s;
+        }
+        __syncthreads();
+        uint32_t c[kScanChunk], off[kScanChunk];
+#pragma unroll
+        for (int i = 0; i < kScanChunk; i++)
+            c[i] = i < (int)nt ? w.tile_cnt[(ull)(t0 + i) * kRadix + d] : 0u;
+        uint32_t run = 0;
+        int first_head = (int)nt;
+#pragma unroll
+        for (int i = 0; i < kScanChunk; i++) {
+            if (i < (int)nt && sh_head[i]) {
+                run = 0;
+                if (first_head == (int)nt) first_head = i;
+            }
+            off[i] = run;
+            run += c[i];
+        }
+        ull* my = w.status + (ull)k * kRadix + d;
+        const bool has_head = first_head < (int)nt;
+        st_relaxed(my, pack_status(has_head ? kFlagInc : kFlagAgg, epoch, run));
+        ull carry = 0;
+        if (first_head > 0) {
+            // Tiles before the chunk's first bucket start continue a bucket
+            // from earlier chunks: look back for its running count.
+            uint32_t j = k - 1;
+            uint32_t spins = 0;
+            while (true) {
+                const ull sv = ld_relaxed(w.status + (ull)j * kRadix + d);
+                const int ep = (int)((sv >> 56) & 0x3F);
+                const ull flag = sv & (3ull << 62);
+                if (ep != epoch || flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        LEY_FAIL(w.err, kErrTimeout);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(64);
+                    continue;
+                }
+                carry += sv & kValMask;
+                if (flag == kFlagInc || j == 0) break;
+                j--;
+            }
+            if (!has_head) st_relaxed(my, pack_status(kFlagInc, epoch, carry + run));
+        }
+#pragma unroll
+        for (int i = 0; i < kScanChunk; i++) {
+            if (i < (int)nt) {
+                const uint32_t o = off[i] + (i < first_head ? (uint32_t)carry : 0u);
+                w.tile_cnt[(ull)(t0 + i) * kRadix + d] = o;
+                if (sh_last[i] && sh_own[i] < nseg)
+                    w.hist[p][(ull)sh_own[i] * kRadix + d] = o + c[i];
+            }
+        }
     }
 }
 
@@ -328,7 +452,7 @@ k_hist(Work w, KeySpec ks, int L) {
 __device__ void emit_fin(const Work& w, ull start, uint32_t count, int digit, int buf, int flags) {
     ull slot = atomicAdd(&w.ctl->fin_count, 1ull);
     if (slot >= w.cap_fin) {
-        atomicOr(w.err, kErrCapacity);
+        LEY_FAIL(w.err, kErrCapacity);
         return;
     }
     FinTask f;
@@ -343,7 +467,7 @@ __device__ void emit_fin(const Work& w, ull start, uint32_t count, int digit, in
 // Appends a bucket to the next level's big list (called by a whole warp with
 // the same arguments): its slot and first tile come from one 64-bit atomic,
 // so slots and tiles are numbered in the same order; the lanes fill the
-// tile-owner table and clear the bucket's histogram.
+// tile-owner table.
 __device__ void append_big_warp(const Work& w, int L1, ull start, uint32_t count, int digit,
                                 int buf) {
     const int q = L1 & 1, lane = threadIdx.x & 31;
@@ -354,7 +478,7 @@ __device__ void append_big_warp(const Work& w, int L1, ull start, uint32_t count
     const ull slot = pk >> kPackShift;
     const ull tb = pk & kPackMask;
     if (slot >= w.cap_seg || tb + nt > w.cap_tiles) {
-        if (lane == 0) atomicOr(w.err, kErrCapacity);
+        if (lane == 0) LEY_FAIL(w.err, kErrCapacity);
         return;
     }
     if (lane == 0) {
@@ -373,9 +497,6 @@ __device__ void append_big_warp(const Work& w, int L1, ull start, uint32_t count
         w.diff[q][slot] = z;
     }
     for (uint32_t i = lane; i < nt; i += 32) w.seg_tile_owner[q][tb + i] = (uint32_t)slot;
-    uint4* h = reinterpret_cast<uint4*>(w.hist[q] + slot * kRadix);
-    h[lane] = make_uint4(0, 0, 0, 0);
-    h[lane + 32] = make_uint4(0, 0, 0, 0);
 }
 
 // One warp per bucket of level L's big list (Algorithm 1's control flow):
@@ -394,12 +515,13 @@ k_classify(Work w, KeySpec ks, int L) {
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
     if (nseg > w.cap_seg) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.err, kErrCapacity);
+        if (threadIdx.x == 0 && blockIdx.x == 0) LEY_FAIL(w.err, kErrCapacity);
         return;
     }
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
         const Seg sg = w.segs[p][s];
+        if (lane == 0) w.seg_pass[p][s] = kNoPass;
         if (sg.count <= (uint32_t)kSmall) {
             if (lane == 0) emit_fin(w, sg.start, sg.count, sg.digit, sg.buf, 0);
             continue;
@@ -425,21 +547,14 @@ k_classify(Work w, KeySpec ks, int L) {
             }
             continue;
         }
-        const uint32_t nt = ceil_div_u64(sg.count, kPassTile);
-        ull pk = 0;
-        if (lane == 0) pk = atomicAdd(&w.ctl->lvl[L].pass_packed, (1ull << kPackShift) | (ull)nt);
-        pk = __shfl_sync(0xffffffffu, pk, 0);
-        const uint32_t e = (uint32_t)(pk >> kPackShift);
-        const ull tb = pk & kPackMask;
-        if (e >= w.cap_seg || tb + nt > w.cap_tiles) {
-            if (lane == 0) atomicOr(w.err, kErrCapacity);
+        ull e = 0;
+        if (lane == 0) e = atomicAdd(&w.ctl->lvl[L].pass_count, 1ull);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (e >= w.cap_seg) {
+            if (lane == 0) LEY_FAIL(w.err, kErrCapacity);
             continue;
         }
-        if (lane == 0) {
-            w.pass_slot[e] = s;
-            w.pass_tile_base[e] = (uint32_t)tb;
-        }
-        for (uint32_t i = lane; i < nt; i += 32) w.pass_tile_owner[tb + i] = e;
+        if (lane == 0) w.seg_pass[p][s] = (uint32_t)e;
         // Exclusive scan over the 256 bins (lane l owns bins 8l..8l+7).
         uint32_t incl = sum;
 #pragma unroll
@@ -448,7 +563,7 @@ k_classify(Work w, KeySpec ks, int L) {
             if (lane >= o) incl += y;
         }
         uint32_t off8[8], run = incl - sum;
-        uint32_t* bb = w.bucket_base + (ull)e * kRadix;
+        uint32_t* bb = w.bucket_base + e * kRadix;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             off8[k] = run;
@@ -514,7 +629,7 @@ k_classify(Work w, KeySpec ks, int L) {
         base = __shfl_sync(0xffffffffu, base, 0);
         for (uint32_t i = lane; i < ng; i += 32) {
             if (base + i >= w.cap_fin) {
-                atomicOr(w.err, kErrCapacity);
+                LEY_FAIL(w.err, kErrCapacity);
                 break;
             }
             const uint32_t gc = sh_gc[threadIdx.x >> 5][i];
@@ -533,34 +648,29 @@ k_classify(Work w, KeySpec ks, int L) {
 // Partition mode (one round of Algorithm 1 only): the single top segment is
 // scattered on its digit whatever its histogram, and nothing recurses.
 __global__ void k_classify_partition(Work w) {
-    const Seg sg = w.segs[0][0];
-    const uint32_t nt = ceil_div_u64(sg.count, kPassTile);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x)
-        w.pass_tile_owner[i] = 0;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    w.ctl->lvl[0].pass_packed = (1ull << kPackShift) | nt;
-    w.pass_slot[0] = 0;
-    w.pass_tile_base[0] = 0;
-    uint32_t off = 0;
-    for (int v = 0; v < kRadix; v++) {
-        w.bucket_base[v] = off;
-        off += w.hist[0][v];
+    if (blockIdx.x != 0) return;
+    const int d = threadIdx.x;
+    if (d == 0) {
+        w.ctl->lvl[0].pass_count = 1;
+        w.seg_pass[0][0] = 0;
+    }
+    // exclusive scan of the 256 bucket sizes (one thread: 256 adds)
+    if (d == 0) {
+        uint32_t off = 0;
+        for (int v = 0; v < kRadix; v++) {
+            w.bucket_base[v] = off;
+            off += w.hist[0][v];
+        }
     }
 }
 
 // ------------------------------------------------------------------ pass
 
-constexpr ull kFlagAgg = 1ull << 62;
-constexpr ull kFlagInc = 2ull << 62;
-constexpr ull kValMask = (1ull << 56) - 1;
-
-__device__ __forceinline__ ull pack_status(ull flag, int epoch, ull val) {
-    return flag | ((ull)epoch << 56) | (val & kValMask);
-}
-
-// One scatter pass of Algorithm 1 over every big bucket of level L.  A CTA
-// takes 4096-tuple tiles in order from a counter, so every predecessor of a
-// tile is already running (forward progress of the look-back).
+// One scatter pass of Algorithm 1 over every big bucket scattered at level L
+// (ParallelRadixSort): tile t of a bucket writes each of its digit runs to
+//   bucket start + bucket_base[digit] + tile offset[digit] (from k_scan),
+// after ranking its tuples stably by digit and staging them in shared memory
+// so that every run is written contiguously (cache-aware scattering).
 __global__ void __launch_bounds__(kPassThreads, 2)
 k_pass(Work w, KeySpec ks, int L) {
     extern __shared__ uint4 stage[];                 // kPassTile tuples
@@ -568,46 +678,41 @@ k_pass(Work w, KeySpec ks, int L) {
     __shared__ uint32_t loc_off[kRadix];
     __shared__ ull gbase[kRadix];
     __shared__ uint32_t scan_tot[kRadix / 32];
-    __shared__ uint32_t sh_tile;
-    __shared__ int sh_bad;
 
     const int p = L & 1;
-    const ull pk = w.ctl->lvl[L].pass_packed;
-    const uint32_t npass = (uint32_t)(pk >> kPackShift);
-    const uint32_t ntiles = (uint32_t)(pk & kPackMask);
-    if (ntiles > w.cap_tiles || npass > w.cap_seg) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.err, kErrCapacity);
+    const ull packed = w.ctl->lvl[L].big_packed;
+    const uint32_t nseg = (uint32_t)(packed >> kPackShift);
+    const uint32_t ntiles = (uint32_t)(packed & kPackMask);
+    if (ntiles > w.cap_tiles || nseg > w.cap_seg) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) LEY_FAIL(w.err, kErrCapacity);
         return;
     }
-    const int epoch = L + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
     LEY_PHASE_BEGIN;
-    while (true) {
-        __syncthreads();
-        LEY_PHASE(0);
-        if (tid == 0) {
-            sh_tile = atomicAdd(&w.ctl->lvl[L].pass_tile_ctr, 1u);
-            sh_bad = 0;
-        }
-        for (int i = tid; i < kPassWarps * kRadix; i += kPassThreads) (&wcnt[0][0])[i] = 0;
-        __syncthreads();
-        const uint32_t t = sh_tile;
-        if (t >= ntiles) break;
-        LEY_PHASE(1);
-        const uint32_t e = w.pass_tile_owner[t];
-        const uint32_t tile0 = w.pass_tile_base[e];
-        const Seg sg = w.segs[p][w.pass_slot[e]];
-        if (e >= npass || sg.start + sg.count > w.n || t < tile0 || sg.buf > 1) {
-            if (tid == 0) atomicOr(w.err, kErrCapacity);  // never for a valid list
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t s = w.seg_tile_owner[p][t];
+        const uint32_t e = s < nseg ? w.seg_pass[p][s] : kNoPass;
+        if (e == kNoPass) continue;  // bucket not scattered at this level
+        const Seg sg = w.segs[p][s];
+        const uint32_t tile0 = w.seg_tile_base[p][s];
+        if (sg.start + sg.count > w.n || t < tile0 || sg.buf > 1 || e >= w.cap_seg) {
+            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);  // never for a valid list
             continue;
         }
+        __syncthreads();  // previous tile's shared state is no longer read
+        LEY_PHASE(0);
+        for (int i = tid; i < kPassWarps * kRadix; i += kPassThreads) (&wcnt[0][0])[i] = 0;
         const uint32_t lt = t - tile0;
         const ull base = sg.start + (ull)lt * kPassTile;
         const uint32_t m = min((uint32_t)kPassTile, sg.count - lt * (uint32_t)kPassTile);
         const uint4* src = w.tup[sg.buf];
         uint4* dst = w.tup[sg.buf ^ 1];
         const int d = sg.digit;
+        ull gb = 0;
+        if (tid < kRadix)
+            gb = sg.start + w.bucket_base[(ull)e * kRadix + tid] +
+                 w.tile_cnt[(ull)t * kRadix + tid];
 
         // Warp `warp` owns items [warp*256, warp*256+256); item k of a lane
         // is at warp*256 + k*32 + lane, so the k-major order is input order
@@ -619,6 +724,7 @@ k_pass(Work w, KeySpec ks, int L) {
             uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
             v[k] = idx < m ? src[base + idx] : make_uint4(0, 0, 0, 0);
         }
+        __syncthreads();  // counters zeroed
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
             const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
@@ -627,78 +733,49 @@ k_pass(Work w, KeySpec ks, int L) {
             rd[k] = (warp_rank(wcnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
         }
         __syncthreads();
-        LEY_PHASE(2);
+        LEY_PHASE(1);
         uint32_t tile_cnt = 0, incl = 0;
-        ull excl = 0;
         if (tid < kRadix) {
             // Thread `tid` owns digit tid: exclusive offsets over warps, then
-            // the tile's count is published for the look-back of later tiles.
+            // the tile-local offset of each digit's run.
             const int dig = tid;
 #pragma unroll
             for (int ww = 0; ww < kPassWarps; ww++) {
-                uint32_t c = wcnt[ww][dig];
+                const uint32_t c = wcnt[ww][dig];
                 wcnt[ww][dig] = tile_cnt;
                 tile_cnt += c;
             }
-            ull* my = w.status + (ull)t * kRadix + dig;
-            if (lt == 0) {
-                st_relaxed(my, pack_status(kFlagInc, epoch, tile_cnt));
-            } else {
-                st_relaxed(my, pack_status(kFlagAgg, epoch, tile_cnt));
-                // Decoupled look-back (Merrill & Garland): walk predecessors
-                // of this bucket, summing aggregates until an inclusive prefix.
-                uint32_t j = t - 1;
-                uint32_t spins = 0;
-                while (true) {
-                    ull s = ld_relaxed(w.status + (ull)j * kRadix + dig);
-                    int ep = (int)((s >> 56) & 0x3F);
-                    ull flag = s & (3ull << 62);
-                    if (ep != epoch || flag == 0) {
-                        if (++spins > kSpinLimit) {
-                            atomicOr(w.err, kErrTimeout);
-                            sh_bad = 1;
-                            break;
-                        }
-                        if (spins > 32) __nanosleep(64);
-                        continue;
-                    }
-                    excl += s & kValMask;
-                    if (flag == kFlagInc || j == tile0) break;
-                    j--;
-                }
-                st_relaxed(my, pack_status(kFlagInc, epoch, excl + tile_cnt));
-            }
-            // Exclusive scan of the tile's digit counts: local offsets.
             incl = tile_cnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
             if (lane == 31) scan_tot[warp] = incl;
         }
         __syncthreads();
-        LEY_PHASE(3);
         if (tid < kRadix) {
             uint32_t wp = 0;
 #pragma unroll
             for (int ww = 0; ww < kRadix / 32; ww++) wp += ww < warp ? scan_tot[ww] : 0u;
             loc_off[tid] = wp + incl - tile_cnt;
-            gbase[tid] = sg.start + w.bucket_base[(ull)e * kRadix + tid] + excl;
+            gbase[tid] = gb;
         }
         __syncthreads();
-        LEY_PHASE(4);
-
+        LEY_PHASE(2);
         // Stage the tile in shared memory in sorted-by-digit order.
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
             const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
             const uint32_t dk = rd[k] & 0xFFu;
-            if (idx < m) stage[loc_off[dk] + wcnt[warp][dk] + (rd[k] >> 8)] = v[k];
+            const uint32_t pos = loc_off[dk] + wcnt[warp][dk] + (rd[k] >> 8);
+            if (idx < m) {
+                if (pos < (uint32_t)kPassTile) stage[pos] = v[k];
+                else LEY_FAIL(w.err, kErrCapacity);  // inconsistent ranks: never
+            }
         }
         __syncthreads();
-        LEY_PHASE(5);
-        if (sh_bad) continue;
+        LEY_PHASE(3);
         // Write each digit's run contiguously to its bucket.
         const ull seg_end = sg.start + sg.count;
         for (uint32_t i = tid; i < m; i += kPassThreads) {
@@ -706,9 +783,9 @@ k_pass(Work w, KeySpec ks, int L) {
             const uint32_t dd = digit_of(tv, d);
             const ull pos = gbase[dd] + (i - loc_off[dd]);
             if (pos >= sg.start && pos < seg_end) dst[pos] = tv;
-            else atomicOr(w.err, kErrCapacity);
+            else LEY_FAIL(w.err, kErrCapacity);
         }
-        LEY_PHASE(6);
+        LEY_PHASE(4);
     }
 }
 
@@ -764,7 +841,7 @@ __device__ __forceinline__ void queue_push(FinShared& S, uint32_t s, uint32_t c,
     atomicAdd(&S.q_pending, 1);  // counted before it can be claimed
     const int slot = atomicAdd(&S.q_tail, 1);
     if (slot >= kFinQueue) {  // cannot happen (see kFinQueue); report and drop
-        atomicOr(err, kErrCapacity);
+        LEY_FAIL(err, kErrCapacity);
         atomicSub(&S.q_pending, 1);
         return;
     }
@@ -782,15 +859,16 @@ __device__ __forceinline__ void stack_push(FinShared& S, uint32_t s, uint32_t c,
         S.bs_meta[slot] = s | (c << 16);
         S.bs_dig[slot] = (uint8_t)d;
     } else {
-        atomicOr(err, kErrCapacity);
+        LEY_FAIL(err, kErrCapacity);
     }
 }
 
-// Sub-bucket of `c2` tuples at B[s2..): finished here by comparison ranking
-// when tiny, else queued for a warp (<= kWarpMax) or for the whole CTA.
-// Block-wide stable counting pass on B[r0, r0+c) -- or on the c tuples at
-// gsrc, staged into B[0, c) -- from digit d0 on (SingleThreadRadixSort of
-// Algorithm 1, one CTA instead of one thread).
+// Block-wide stable counting pass on B[r0, r0+c) -- or, with FROM_GLOBAL,
+// on the c tuples at gsrc, staged into B[r0, r0+c) -- from digit d0 on
+// (SingleThreadRadixSort of Algorithm 1, one CTA instead of one thread).
+// Its sub-buckets are finished here by comparison ranking when tiny, else
+// queued for a warp (<= kWarpMax) or pushed for the whole CTA.
+template <bool FROM_GLOBAL>
 __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0,
                                uint32_t c, int d0, const KeySpec& ks, uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -800,11 +878,14 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
     if (tid < 3) S.d3[tid] = 0;
 #pragma unroll
     for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
-    const uint4 ref = gsrc ? gsrc[0] : B[r0];
+    const uint4 ref = FROM_GLOBAL ? gsrc[0] : B[r0];
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
         const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
-        v[k] = idx < c ? (gsrc ? gsrc[idx] : B[r0 + idx]) : ref;
+        if (FROM_GLOBAL)
+            v[k] = idx < c ? gsrc[idx] : ref;
+        else
+            v[k] = idx < c ? B[r0 + idx] : ref;
     }
     ull dhi = 0;
     uint32_t dlo = 0;
@@ -815,7 +896,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
     }
     __syncthreads();  // counters zeroed, all reads of B done
 #ifdef LEY_PHASE_TIMING
-    if (gsrc && threadIdx.x == 0) atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
+    if (FROM_GLOBAL && threadIdx.x == 0) atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
 #endif
     warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, S.d3);
     __syncthreads();
@@ -826,7 +907,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         for (int k = 0; k < kFinItems; k++) {
             const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
             if (idx < c) {
-                if (gsrc) B[r0 + idx] = v[k];
+                if (FROM_GLOBAL) B[r0 + idx] = v[k];
                 S.order[r0 + idx] = (uint16_t)(r0 + idx);
             }
         }
@@ -868,7 +949,11 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
     for (int k = 0; k < kFinItems; k++) {
         const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
         const uint32_t dk = rd[k] & 0xFFu;
-        if (idx < c) B[r0 + S.sb_off[dk] + S.cnt[warp][dk] + (rd[k] >> 8)] = v[k];
+        const uint32_t pos = r0 + S.sb_off[dk] + S.cnt[warp][dk] + (rd[k] >> 8);
+        if (idx < c) {
+            if (pos < r0 + c) B[pos] = v[k];
+            else LEY_FAIL(err, kErrCapacity);  // inconsistent ranks: never
+        }
     }
     __syncthreads();
     {
@@ -878,7 +963,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         else if (sc > (uint32_t)kTiny) queue_push(S, s2, sc, ds + 1, err);
     }
 #ifdef LEY_PHASE_TIMING
-    if (gsrc && threadIdx.x == 0) atomicAdd(&g_ley_phase[21], (unsigned long long)clock64());
+    if (FROM_GLOBAL && threadIdx.x == 0) atomicAdd(&g_ley_phase[21], (unsigned long long)clock64());
 #endif
     // Tiny sub-buckets: rank by comparison (ComparisonSort of Algorithm 1).
     for (uint32_t i = tid; i < c; i += kFinThreads) {
@@ -887,7 +972,9 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         const uint32_t sc = S.sb_cnt[dd];
         if (sc <= (uint32_t)kTiny) {
             const uint32_t so = r0 + S.sb_off[dd];
-            S.order[so + cmp_rank(B, so, sc, tv, ks.lo_mask)] = (uint16_t)(r0 + i);
+            const uint32_t r = cmp_rank(B, so, sc, tv, ks.lo_mask);
+            if (r < sc) S.order[so + r] = (uint16_t)(r0 + i);
+            else LEY_FAIL(err, kErrCapacity);  // tv not in its sub-bucket: never
         }
     }
 }
@@ -959,7 +1046,11 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
     for (int k = 0; k < kFinItems; k++) {
         const uint32_t idx = k * 32 + lane;
         const uint32_t dk = rd[k] & 0xFFu;
-        if (idx < c) B[s + off[dk] + (rd[k] >> 8)] = v[k];
+        const uint32_t pos = s + off[dk] + (rd[k] >> 8);
+        if (idx < c) {
+            if (pos < s + c) B[pos] = v[k];
+            else LEY_FAIL(err, kErrCapacity);  // inconsistent ranks: never
+        }
     }
     __syncwarp();
 #pragma unroll
@@ -971,7 +1062,9 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
         const uint32_t sc = cnt[dd];
         if (sc <= (uint32_t)kTiny) {
             const uint32_t so = s + off[dd];
-            S.order[so + cmp_rank(B, so, sc, tv, ks.lo_mask)] = (uint16_t)(s + i);
+            const uint32_t r = cmp_rank(B, so, sc, tv, ks.lo_mask);
+            if (r < sc) S.order[so + r] = (uint16_t)(s + i);
+            else LEY_FAIL(err, kErrCapacity);  // tv not in its sub-bucket: never
         }
     }
     __syncwarp();
@@ -994,7 +1087,7 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
                 uint32_t spins = 0;
                 while (*(volatile uint8_t*)&S.q_ready[slot] == 0) {
                     if (++spins > kSpinLimit) {
-                        atomicOr(err, kErrTimeout);
+                        LEY_FAIL(err, kErrTimeout);
                         ok = 0;
                         break;
                     }
@@ -1016,7 +1109,7 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
             if (ok && s0 + c0 <= (uint32_t)kSmall && c0 <= (uint32_t)kWarpMax)
                 fin_warp_sort(B, S, s0, c0, (int)dg, ks, err);
             else if (lane == 0)
-                atomicOr(err, kErrCapacity);
+                LEY_FAIL(err, kErrCapacity);
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
@@ -1027,7 +1120,7 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
             pending = __shfl_sync(0xffffffffu, pending, 0);
             if (pending == 0) break;
             if (++idle > kSpinLimit) {
-                if (lane == 0) atomicOr(err, kErrTimeout);
+                if (lane == 0) LEY_FAIL(err, kErrTimeout);
                 break;
             }
             __nanosleep(32);
@@ -1057,7 +1150,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
         LEY_PHASE(11);
         const FinTask tk = w.fin[ti];
         if (tk.start + tk.count > w.n || tk.buf > 1) {  // never for a valid task list
-            if (tid == 0) atomicOr(w.err, kErrCapacity);
+            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
             continue;
         }
         const uint4* src = w.tup[tk.buf] + tk.start;
@@ -1066,10 +1159,10 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             continue;
         }
         if (tk.count > (uint32_t)kSmall) {  // never produced by k_classify
-            if (tid == 0) atomicOr(w.err, kErrCapacity);
+            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
             continue;
         }
-        fin_block_pass(B, S, src, 0, tk.count, tk.digit, ks, w.err);
+        fin_block_pass<true>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
         __syncthreads();
         LEY_PHASE(12);
         while (true) {
@@ -1084,17 +1177,27 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             __syncthreads();
             if (tid == 0) S.bs_n = top;
             if ((meta & 0xFFFFu) + (meta >> 16) > (uint32_t)kSmall) {
-                if (tid == 0) atomicOr(w.err, kErrCapacity);
+                if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
                 continue;
             }
-            fin_block_pass(B, S, nullptr, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
+            fin_block_pass<false>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
         }
         LEY_PHASE(13);
         // Coalesced write of the task's final order.
         for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
             uint32_t o = S.order[j];
             if (o >= tk.count) {  // a position left unset: report, stay in bounds
-                atomicOr(w.err, kErrCapacity);
+                LEY_FAIL(w.err, kErrCapacity);
+#ifdef LEY_PHASE_TIMING
+                if (atomicCAS(&g_ley_phase[40], 0ull, 1ull) == 0ull) {
+                    g_ley_phase[41] = tk.start;
+                    g_ley_phase[42] = tk.count;
+                    g_ley_phase[43] = tk.digit | (tk.flags << 8) | (tk.buf << 16);
+                    g_ley_phase[44] = j;
+                    g_ley_phase[45] = o;
+                    g_ley_phase[46] = ti;
+                }
+#endif
                 o = 0;
             }
             emit(tk.start + j, B[o]);
@@ -1127,17 +1230,15 @@ namespace ley {
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, ull n, uint32_t rec,
                                    KeySpec ks, const Work& w, int hist_digit) {
     if (rec == 100)
-        k_extract_records<100><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w.tup[0], w.hist[0],
-                                                             w.diff[0], hist_digit);
+        k_extract_records<100><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit);
     else
-        k_extract_records<0><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w.tup[0], w.hist[0],
-                                                           w.diff[0], hist_digit);
+        k_extract_records<0><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit);
     return cudaGetLastError();
 }
 
 cudaError_t launch_extract_pairs(const LaunchCfg& c, const uint64_t* keys, const uint32_t* idx,
                                  ull n, KeySpec, const Work& w) {
-    k_extract_pairs<<<c.grid, 256, 0, c.stream>>>(keys, idx, n, w.tup[0], w.hist[0], w.diff[0]);
+    k_extract_pairs<<<c.grid, 256, 0, c.stream>>>(keys, idx, n, w);
     return cudaGetLastError();
 }
 
@@ -1151,13 +1252,18 @@ cudaError_t launch_hist(const LaunchCfg& c, const Work& w, KeySpec ks, int level
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan(const LaunchCfg& c, const Work& w, int level) {
+    k_scan<<<c.grid, kRadix, 0, c.stream>>>(w, level);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int level) {
     k_classify<<<c.grid, 128, 0, c.stream>>>(w, ks, level);
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify_partition(cudaStream_t s, const Work& w) {
-    k_classify_partition<<<64, 256, 0, s>>>(w);
+    k_classify_partition<<<1, 32, 0, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -1228,6 +1334,8 @@ int blocks_per_sm(KernelKind k) {
         g_bps[KK_EXTRACT_PAIRS] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_hist, kHistThreads, 0);
         g_bps[KK_HIST] = v > 0 ? v : 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_scan, kRadix, 0);
+        g_bps[KK_SCAN] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pass, kPassThreads,
                                                       kernel_smem(KK_PASS));
         g_bps[KK_PASS] = v > 0 ? v : 1;
