@@ -111,6 +111,32 @@ const char* ley_status_string(ley_status s);
  */
 ley_status ley_last_device_status(ley_stream_t stream);
 
+/*
+ * Allocation-free record sort, for callers that cannot allocate device
+ * memory: for example an application whose device memory is entirely owned by
+ * its own pool allocator, or a latency-bound caller for which a cudaMalloc
+ * (which can wait for the whole device) is not acceptable.  The paper has no
+ * counterpart; this is an interface of this library only.
+ *
+ * Same sort and arguments as ley_sort_records with both buffers on the device
+ * (16-byte aligned, not overlapping), but the call never allocates or frees:
+ * its scratch is one fixed device array of 12 MiB inside this library, which
+ * every GPU that loads the library holds until the process exits.
+ *   n           at most LEY_NOALLOC_MAX_RECORDS; larger n returns LEY_ENOMEM
+ *               before any work.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  The call waits for its work on `stream` and returns its device-side
+ * status (LEY_ETIMEOUT if a bounded wait gave up).  All calls share the one
+ * array and each leaves its contents behind: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.
+ */
+#define LEY_NOALLOC_MAX_RECORDS 262144ull
+
+ley_status ley_sort_records_noalloc(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                                    uint32_t key_bytes, ley_stream_t stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t ley_launch_count(void);
 

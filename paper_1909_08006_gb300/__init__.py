@@ -22,9 +22,11 @@ __all__ = [
     "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
+    "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
+LEY_NOALLOC_MAX_RECORDS = 262144
 
 
 class LeyError(RuntimeError):
@@ -71,6 +73,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_profile_enable.restype = ctypes.c_int
     lib.ley_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
     lib.ley_profile_read.restype = ctypes.c_int
+    lib.ley_sort_records_noalloc.argtypes = [vp, vp, u64, u32, u32, vp]
+    lib.ley_sort_records_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -134,6 +138,23 @@ def ley_sort_records(inp, out, n: int | None = None, rec_bytes: int | None = Non
     st = _lib.ley_sort_records(_addr(inp), _addr(out), n, rec_bytes, key_bytes, mem_budget,
                                _stream(stream, inp, out))
     return _check(st, "ley_sort_records")
+
+
+def ley_sort_records_noalloc(inp, out, n: int | None = None, rec_bytes: int | None = None,
+                             key_bytes: int = 10, stream=None) -> int:
+    """Allocation-free form of ley_sort_records for callers that cannot
+    allocate device memory (their device memory is owned by their own pool,
+    or a cudaMalloc would stall them).  Device buffers only, at most
+    LEY_NOALLOC_MAX_RECORDS records; scratch is one fixed array inside the
+    library shared by all calls, so calls must not overlap on the GPU.  Waits
+    for its work and returns its device-side status."""
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
+    st = _lib.ley_sort_records_noalloc(_addr(inp), _addr(out), n, rec_bytes, key_bytes,
+                                       _stream(stream, inp, out))
+    return _check(st, "ley_sort_records_noalloc")
 
 
 def ley_sort_keys_index(keys_in, idx_in, keys_out, idx_out, n: int | None = None,

@@ -534,3 +534,133 @@ int ley_profile_read(ley_kernel_time* out, int max) {
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free sort
+//
+// ley_sort_records_noalloc serves callers that cannot allocate device memory:
+// for example an application whose device memory is entirely owned by its own
+// pool allocator, or a latency-bound caller for which a cudaMalloc (which can
+// wait for the whole device) is not acceptable.  Its scratch is one file-scope
+// device array, so the call itself never allocates or frees.
+
+namespace ley {
+
+// Largest input of the allocation-free sort, and its fixed scratch size: the
+// workspace of an internal sort of that many records plus one 256-byte block
+// at the end for the call's device status words.
+constexpr unsigned long long kNoAllocMaxRecords = LEY_NOALLOC_MAX_RECORDS;
+constexpr size_t kNoAllocBytes = 12u << 20;
+constexpr size_t kNoAllocStatusBytes = 256;
+
+// The scratch array.  It lives in every device's copy of this library's
+// device code, from the time that code is loaded until the process exits.
+// Host code must not use its name as an address: it resolves the device
+// address with cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDev {
+    bool init = false;
+    char* base = nullptr;   // device address of g_noalloc_scratch
+    int sms = 0;
+};
+static NoAllocDev g_noalloc[64];
+static std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: the scratch array's device
+// address and the SM count.  Allocates nothing.
+static NoAllocDev* noalloc_setup() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDev& s = g_noalloc[d];
+    if (!s.init) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+            return nullptr;
+        s.base = static_cast<char*>(p);
+        s.sms = sms;
+        s.init = true;
+    }
+    return &s;
+}
+
+// The internal record sort of enqueue_sort, with all scratch at `base` and
+// device errors latched in `err` (no per-device state of the library used).
+static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const Layout& L,
+                                          cudaStream_t st, int sms, uint32_t* err) {
+    Work w = make_work(base, L, a.n, err);
+    const KeySpec ks = record_keyspec(a.kb);
+    LEY_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
+    LEY_TRY(cudaMemsetAsync(w.diff[0], 0, sizeof(Diff), st));
+    LEY_TRY(cudaMemsetAsync(w.status, 0, L.cap_chunks * kRadix * sizeof(ull), st));
+    LEY_TRY(launch_init(st, w, a.n, 0));
+    {
+        LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
+        LEY_TRY(launch_extract_records(c, a.in, a.n, a.rec, ks, w, 0));
+    }
+    const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
+    const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
+    const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
+    const LaunchCfg cc{2 * sms, 128, 0, st};
+    for (int lvl = 0; lvl < ks.ndig; lvl++) {
+        if (lvl > 0) LEY_TRY(launch_hist(ch, w, ks, lvl));
+        LEY_TRY(launch_scan(cs, w, lvl));
+        LEY_TRY(launch_classify(cc, w, ks, lvl));
+        LEY_TRY(launch_pass(cp, w, ks, lvl));
+    }
+    LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+    LEY_TRY(launch_finish_records(cf, w, ks));
+    const int gv = a.rec == 100 ? gather_variant() : 0;
+    const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
+                                       : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
+    LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
+    LEY_TRY(launch_gather_err(cg, a.in, a.out, w.perm, a.n, a.rec, gv, err));
+    return LEY_OK;
+}
+
+}  // namespace ley
+
+extern "C" ley_status ley_sort_records_noalloc(const void* in, void* out, uint64_t n,
+                                               uint32_t rec_bytes, uint32_t key_bytes,
+                                               ley_stream_t stream) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u))
+        return LEY_EUNSUPPORTED;
+    if (n > kNoAllocMaxRecords) return LEY_ENOMEM;
+    if (n == 0) return LEY_OK;
+    if (!in || !out) return LEY_EINVAL;
+    const ull bytes = n * rec_bytes;
+    if (overlaps(in, bytes, out, bytes)) return LEY_EINVAL;
+    if (mem_kind(in) != MK_DEVICE || mem_kind(out) != MK_DEVICE) return LEY_EINVAL;
+    if (!aligned16(in) || !aligned16(out)) return LEY_EINVAL;
+    NoAllocDev* dev = noalloc_setup();
+    if (!dev) return LEY_ECUDA;
+    const Layout L = make_layout(n, true);
+    if (L.total + kNoAllocStatusBytes > kNoAllocBytes) return LEY_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t* err = reinterpret_cast<uint32_t*>(dev->base + kNoAllocBytes - kNoAllocStatusBytes);
+    // The array keeps the previous call's contents: clear the status words
+    // (the sort itself clears its counters, statuses and digit masks).
+    if (cudaMemsetAsync(err, 0, kNoAllocStatusBytes, st) != cudaSuccess) return LEY_ECUDA;
+    SortArgs a{};
+    a.mode = MODE_RECORDS;
+    a.in = static_cast<const uint8_t*>(in);
+    a.out = static_cast<uint8_t*>(out);
+    a.n = n;
+    a.rec = rec_bytes;
+    a.kb = key_bytes;
+    const ley_status s = enqueue_records_noalloc(a, dev->base, L, st, dev->sms, err);
+    if (s != LEY_OK) return s;
+    uint32_t ev[2] = {0, 0};
+    if (cudaMemcpyAsync(ev, err, sizeof(ev), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return LEY_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LEY_ECUDA;
+    if (ev[0] & kErrTimeout) return LEY_ETIMEOUT;
+    if (ev[0] & kErrCapacity) return LEY_ENOMEM;
+    return LEY_OK;
+}

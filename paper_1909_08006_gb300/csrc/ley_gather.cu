@@ -318,4 +318,19 @@ cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
     return cudaGetLastError();
 }
 
+// Same kernels as launch_gather, with the device status word given by the
+// caller instead of the library's per-device word.
+cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
+                              const uint32_t* perm, ull n, uint32_t rec, int variant,
+                              uint32_t* err) {
+    if (rec == kRec && variant == 1) {
+        k_gather100_tma<<<c.grid, kTmaWarps * 32, tma_smem(), c.stream>>>(in, out, perm, n, err);
+    } else if (rec == kRec) {
+        k_gather100<<<c.grid, kGatherWarps * 32, 0, c.stream>>>(in, out, perm, n, err);
+    } else {
+        k_gather_generic<<<c.grid, 256, 0, c.stream>>>(in, out, perm, n, rec);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace ley

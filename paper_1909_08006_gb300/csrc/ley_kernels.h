@@ -30,6 +30,9 @@ cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, u
 cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
                           const uint32_t* perm, unsigned long long n, uint32_t rec_bytes,
                           int variant);
+cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
+                              const uint32_t* perm, unsigned long long n, uint32_t rec_bytes,
+                              int variant, uint32_t* err);
 cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsigned long long n,
                                  uint32_t* order_out, unsigned long long* hist_out);
 
