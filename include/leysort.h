@@ -95,6 +95,23 @@ ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
                                  uint64_t* hist_out, ley_stream_t stream);
 
 /*
+ * K-way merge of sorted runs: the merge stage of the external sort
+ * (Section 3.2, Figure 1: "a K-way merge algorithm"), exposed on its own.
+ *   runs       device, run_start[k] records back to back; run r holds records
+ *              run_start[r] .. run_start[r+1]-1 and must already be sorted by
+ *              key (stable), e.g. by ley_sort_records.
+ *   run_start  host array of k+1 record offsets, run_start[0] = 0, non-decreasing
+ *              (empty runs allowed); read before the call returns.
+ *   k          1..128.
+ *   out        device, run_start[k] records: the stable merge, equal keys
+ *              ordered by run, then by position in the run.
+ * Asynchronous on `stream`.  Unsorted runs give an unspecified order (still a
+ * permutation of the records).
+ */
+ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32_t k, void* out,
+                             uint32_t rec_bytes, uint32_t key_bytes, ley_stream_t stream);
+
+/*
  * Device scratch (bytes) that ley_sort_records would allocate for an internal
  * sort of n records of this geometry.  Host-only; needs no GPU.
  */

@@ -22,7 +22,7 @@ __all__ = [
     "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
-    "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS",
+    "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS", "ley_merge_records",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -73,6 +73,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_profile_enable.restype = ctypes.c_int
     lib.ley_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
     lib.ley_profile_read.restype = ctypes.c_int
+    lib.ley_merge_records.argtypes = [vp, ctypes.POINTER(u64), u32, vp, u32, u32, vp]
+    lib.ley_merge_records.restype = ctypes.c_int
     lib.ley_sort_records_noalloc.argtypes = [vp, vp, u64, u32, u32, vp]
     lib.ley_sort_records_noalloc.restype = ctypes.c_int
     return lib
@@ -180,6 +182,20 @@ def ley_partition_records(inp, digit: int, order_out, hist_out, n: int | None = 
                                     _addr(order_out), _addr(hist_out),
                                     _stream(stream, inp, order_out))
     return _check(st, "ley_partition_records")
+
+
+def ley_merge_records(runs, run_start, out, rec_bytes: int | None = None, key_bytes: int = 10,
+                      stream=None) -> int:
+    """Stable k-way merge of sorted runs stored back to back (run r holds
+    records run_start[r] .. run_start[r+1]-1)."""
+    starts = [int(x) for x in run_start]
+    k = len(starts) - 1
+    if rec_bytes is None:
+        rec_bytes = int(runs.shape[1])
+    arr = (ctypes.c_uint64 * len(starts))(*starts)
+    st = _lib.ley_merge_records(_addr(runs), arr, k, _addr(out), rec_bytes, key_bytes,
+                                _stream(stream, runs, out))
+    return _check(st, "ley_merge_records")
 
 
 def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10) -> int:

@@ -1,5 +1,6 @@
 // C ABI of leysort: argument checks, scratch layout, the launch sequence of
 // the internal sort, and the host-memory (partially in-memory) mode.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -223,39 +224,34 @@ struct SortArgs {
         if ((x) != cudaSuccess) return LEY_ECUDA;    \
     } while (0)
 
-// Queues the whole sort on `st` using scratch at `base` (layout L).
-static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, cudaStream_t st,
-                               DevState* ds) {
-    Work w = make_work(base, L, a.n, ds->err);
-    const KeySpec ks = a.mode == MODE_PAIRS ? pair_keyspec() : record_keyspec(a.kb);
-    const int sms = ds->sms;
+// Stages of one internal sort, all queued on `st` with scratch described by w.
+
+static ley_status stage_prepare(const Work& w, const Layout& L, cudaStream_t st, ull n,
+                                int digit0) {
     LEY_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
     LEY_TRY(cudaMemsetAsync(w.diff[0], 0, sizeof(Diff), st));
     LEY_TRY(cudaMemsetAsync(w.status, 0, L.cap_chunks * kRadix * sizeof(ull), st));
-    const int digit0 = a.mode == MODE_PARTITION ? (int)a.digit : 0;
-    LEY_TRY(launch("init", st, [&] { return launch_init(st, w, a.n, digit0); }));
-    if (a.mode == MODE_PAIRS) {
-        LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_PAIRS), 256, 0, st};
-        LEY_TRY(launch("extract", st, [&] {
-            return launch_extract_pairs(c, a.keys_in, a.idx_in, a.n, ks, w);
-        }));
-    } else {
-        LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
-        LEY_TRY(launch("extract", st, [&] {
-            return launch_extract_records(c, a.in, a.n, a.rec, ks, w, digit0);
-        }));
-    }
+    LEY_TRY(launch("init", st, [&] { return launch_init(st, w, n, digit0); }));
+    return LEY_OK;
+}
+
+// Records [t_begin, t_end) tiles -> tuples and per-tile digit counts.
+static ley_status stage_extract_records(const SortArgs& a, const Work& w, const KeySpec& ks,
+                                        cudaStream_t st, int sms, int digit0, uint32_t t_begin,
+                                        uint32_t t_end) {
+    LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
+    LEY_TRY(launch("extract", st, [&] {
+        return launch_extract_records_tiles(c, a.in, a.n, a.rec, ks, w, digit0, t_begin, t_end);
+    }));
+    return LEY_OK;
+}
+
+// The MSD levels (histogram, offset scan, classify, scatter) and the
+// small-bucket finish; records mode leaves the permutation in w.perm.
+static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const KeySpec& ks,
+                                      cudaStream_t st, int sms) {
     const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
-    if (a.mode == MODE_PARTITION) {
-        LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, 0); }));
-        LEY_TRY(launch("classify", st, [&] { return launch_classify_partition(st, w); }));
-        LEY_TRY(launch("pass", st, [&] { return launch_pass(cp, w, ks, 0); }));
-        LEY_TRY(launch("partition_out", st, [&] {
-            return launch_partition_out(st, sms * 4, w, a.n, a.order_out, a.hist_out);
-        }));
-        return LEY_OK;
-    }
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
     const LaunchCfg cc{2 * sms, 128, 0, st};
     for (int lvl = 0; lvl < ks.ndig; lvl++) {
@@ -274,14 +270,55 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
     }
     LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
     LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
+    return LEY_OK;
+}
+
+// out_base[j - j0] = in[perm[j]] for output records j in [j0, j1).
+static ley_status stage_gather(const SortArgs& a, const uint32_t* perm, cudaStream_t st, int sms,
+                               ull j0, ull j1, uint8_t* out_base) {
+    if (j1 <= j0) return LEY_OK;
     const int gv = a.rec == 100 ? gather_variant() : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
     LEY_TRY(launch("gather", st, [&] {
-        return launch_gather(cg, a.in, a.out, w.perm, a.n, a.rec, gv);
+        return launch_gather(cg, a.in, out_base, perm + j0, j1 - j0, a.n, a.rec, gv);
     }));
     return LEY_OK;
+}
+
+// Queues the whole sort on `st` using scratch at `base` (layout L).
+static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, cudaStream_t st,
+                               DevState* ds) {
+    Work w = make_work(base, L, a.n, ds->err);
+    const KeySpec ks = a.mode == MODE_PAIRS ? pair_keyspec() : record_keyspec(a.kb);
+    const int sms = ds->sms;
+    const int digit0 = a.mode == MODE_PARTITION ? (int)a.digit : 0;
+    ley_status s = stage_prepare(w, L, st, a.n, digit0);
+    if (s != LEY_OK) return s;
+    if (a.mode == MODE_PAIRS) {
+        LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_PAIRS), 256, 0, st};
+        LEY_TRY(launch("extract", st, [&] {
+            return launch_extract_pairs(c, a.keys_in, a.idx_in, a.n, ks, w);
+        }));
+    } else {
+        s = stage_extract_records(a, w, ks, st, sms, digit0, 0, ceil_div_u64(a.n, kPassTile));
+        if (s != LEY_OK) return s;
+    }
+    if (a.mode == MODE_PARTITION) {
+        const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
+        const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
+        LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, 0); }));
+        LEY_TRY(launch("classify", st, [&] { return launch_classify_partition(st, w); }));
+        LEY_TRY(launch("pass", st, [&] { return launch_pass(cp, w, ks, 0); }));
+        LEY_TRY(launch("partition_out", st, [&] {
+            return launch_partition_out(st, sms * 4, w, a.n, a.order_out, a.hist_out);
+        }));
+        return LEY_OK;
+    }
+    s = stage_levels_finish(a, w, ks, st, sms);
+    if (s != LEY_OK || a.mode == MODE_PAIRS) return s;
+    return stage_gather(a, w.perm, st, sms, 0, a.n, a.out);
 }
 
 static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st) {
@@ -301,15 +338,106 @@ static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st
 
 // ------------------------------------------------- host-memory sorting
 
-// Partially in-memory sort (Section 4.1's 20 GB case, the page-cache scatter
-// of Section 3.2): pinned host input and output, the input resident on the
-// device for the sort, the sorted records streamed back.  Blocks.
+// Side streams and events of one host-memory sort (the reader and writer
+// threads of Section 3.2 become two copy streams beside the compute stream).
+struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> evs;
+    bool ok = true;
+    explicit HostPipe(cudaStream_t st) {
+        ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) {
+            cudaEvent_t e = ev();  // side streams start after the caller's prior work
+            ok = e && cudaEventRecord(e, st) == cudaSuccess &&
+                 cudaStreamWaitEvent(h2d, e, 0) == cudaSuccess &&
+                 cudaStreamWaitEvent(d2h, e, 0) == cudaSuccess;
+        }
+    }
+    cudaEvent_t ev() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        evs.push_back(e);
+        return e;
+    }
+    // `to` waits for the work queued so far on `from`.
+    bool order(cudaStream_t from, cudaStream_t to) {
+        cudaEvent_t e = ev();
+        return e && cudaEventRecord(e, from) == cudaSuccess &&
+               cudaStreamWaitEvent(to, e, 0) == cudaSuccess;
+    }
+    ~HostPipe() {
+        if (h2d) cudaStreamSynchronize(h2d);
+        if (d2h) cudaStreamSynchronize(d2h);
+        for (auto e : evs) cudaEventDestroy(e);
+        if (h2d) cudaStreamDestroy(h2d);
+        if (d2h) cudaStreamDestroy(d2h);
+    }
+};
+
+// Streams sorted records to host memory: perm[j0, j1) gathered into two
+// alternating device staging buffers of q records on `st`, each copied to
+// host_out + (j - j0) records on the writer stream as soon as it is full.
+static ley_status stream_out(const SortArgs& a, const uint32_t* perm, ull j0, ull j1,
+                             uint8_t* host_out, uint8_t* const stg[2], ull q, cudaStream_t st,
+                             HostPipe& hp, cudaEvent_t stg_free[2], int sms) {
+    int b = 0;
+    for (ull j = j0; j < j1; j += q, b ^= 1) {
+        const ull je = j + q < j1 ? j + q : j1;
+        if (stg_free[b] && cudaStreamWaitEvent(st, stg_free[b], 0) != cudaSuccess) return LEY_ECUDA;
+        ley_status s = stage_gather(a, perm, st, sms, j, je, stg[b]);
+        if (s != LEY_OK) return s;
+        if (!hp.order(st, hp.d2h)) return LEY_ECUDA;
+        LEY_TRY(cudaMemcpyAsync(host_out + (j - j0) * a.rec, stg[b], (je - j) * a.rec,
+                                cudaMemcpyDeviceToHost, hp.d2h));
+        cudaEvent_t e = hp.ev();
+        if (!e || cudaEventRecord(e, hp.d2h) != cudaSuccess) return LEY_ECUDA;
+        stg_free[b] = e;
+    }
+    return LEY_OK;
+}
+
+// Copies host records [r0, r0+m) to dev, in chunks of whole tiles, and has
+// `st` extract each chunk's tiles as soon as it has landed.
+static ley_status stream_in_extract(const SortArgs& a, const uint8_t* host_in, uint8_t* dev,
+                                    const Work& w, const KeySpec& ks, cudaStream_t st,
+                                    HostPipe& hp, int sms) {
+    const ull chunk = (ull)kPassTile * 256;  // ~100 MB of 100-byte records
+    for (ull c0 = 0; c0 < a.n; c0 += chunk) {
+        const ull c1 = c0 + chunk < a.n ? c0 + chunk : a.n;
+        LEY_TRY(cudaMemcpyAsync(dev + c0 * a.rec, host_in + c0 * a.rec, (c1 - c0) * a.rec,
+                                cudaMemcpyHostToDevice, hp.h2d));
+        if (!hp.order(hp.h2d, st)) return LEY_ECUDA;
+        ley_status s = stage_extract_records(a, w, ks, st, sms, 0, (uint32_t)(c0 / kPassTile),
+                                             ceil_div_u64(c1, kPassTile));
+        if (s != LEY_OK) return s;
+    }
+    return LEY_OK;
+}
+
+static ull staging_records(ull n, uint32_t rec, ull budget) {
+    ull q = (64ull << 20) / rec;  // 64 MB staging buffers
+    if (budget) {
+        const ull cap = budget / (16ull * rec);
+        if (cap < q) q = cap;
+    }
+    if (q < 1024) q = 1024;
+    return q < n ? q : n;
+}
+
+// Partially in-memory sort (Section 4.1's 20 GB case; the page-cache record
+// scatter of Section 3.2): pinned host input and output, the input resident
+// on the device, extraction overlapped with the copy in, and the sorted
+// records streamed back through two staging buffers.  Blocks.  Returns
+// LEY_ENOMEM without touching anything if it does not fit the budget.
 static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t st) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     const ull bytes = a.n * a.rec;
     const Layout L = make_layout(a.n, true);
-    const size_t need = align_up(bytes, 256) * 2 + L.total;
+    const ull q = staging_records(a.n, a.rec, budget);
+    const size_t stg_bytes = align_up(q * a.rec, 256);
+    const size_t need = align_up(bytes, 256) + L.total + 2 * stg_bytes;
     if (budget && need > budget) return LEY_ENOMEM;
     void* dmem = nullptr;
     if (cudaMallocAsync(&dmem, need, st) != cudaSuccess) {
@@ -317,22 +445,287 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         return LEY_ENOMEM;
     }
     char* din = static_cast<char*>(dmem);
-    char* dout = din + align_up(bytes, 256);
-    char* ws = dout + align_up(bytes, 256);
+    char* ws = din + align_up(bytes, 256);
+    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
+                       reinterpret_cast<uint8_t*>(ws + L.total + stg_bytes)};
     ley_status s = LEY_OK;
-    if (cudaMemcpyAsync(din, a.in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) s = LEY_ECUDA;
-    if (s == LEY_OK) {
+    {
+        HostPipe hp(st);
+        if (!hp.ok) s = LEY_ECUDA;
         SortArgs d = a;
         d.in = reinterpret_cast<const uint8_t*>(din);
-        d.out = reinterpret_cast<uint8_t*>(dout);
-        s = enqueue_sort(d, ws, L, st, ds);
+        Work w = make_work(ws, L, a.n, ds->err);
+        const KeySpec ks = record_keyspec(a.kb);
+        if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
+        if (s == LEY_OK) s = stream_in_extract(d, a.in, reinterpret_cast<uint8_t*>(din), w, ks, st, hp, ds->sms);
+        if (s == LEY_OK) s = stage_levels_finish(d, w, ks, st, ds->sms);
+        cudaEvent_t stg_free[2] = {nullptr, nullptr};
+        if (s == LEY_OK) s = stream_out(d, w.perm, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
+        if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
+        cudaFreeAsync(dmem, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
     }
-    if (s == LEY_OK &&
-        cudaMemcpyAsync(a.out, dout, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        s = LEY_ECUDA;
-    cudaFreeAsync(dmem, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return LEY_ECUDA;
     return s;
+}
+
+// Pinned host scratch for the sorted runs of the external sort, kept across
+// calls (pinning tens of GB takes seconds) and grown on demand.
+static std::mutex g_host_scratch_mu;
+static uint8_t* g_host_scratch = nullptr;
+static size_t g_host_scratch_bytes = 0;
+
+static uint8_t* host_scratch(size_t bytes) {
+    if (bytes <= g_host_scratch_bytes) return g_host_scratch;
+    if (g_host_scratch) cudaFreeHost(g_host_scratch);
+    g_host_scratch = nullptr;
+    g_host_scratch_bytes = 0;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_host_scratch = static_cast<uint8_t*>(p);
+    g_host_scratch_bytes = bytes;
+    return g_host_scratch;
+}
+
+// A sorted run in host memory.
+struct HostRun {
+    const uint8_t* base;
+    ull len;
+};
+
+// Elements of run i ordered before the element at position ppos of run prun
+// (key K there) in the order (key, run, position): the k-way co-rank used to
+// cut the merge into independent partitions (Section 3.2's partitioning).
+static ull corank_split(const std::vector<HostRun>& runs, size_t i, const uint8_t* K, size_t prun,
+                        ull ppos, uint32_t rec, uint32_t kb) {
+    if (i == prun) return ppos;
+    const bool upper = i < prun;  // equal keys of lower runs come first
+    ull lo = 0, hi = runs[i].len;
+    while (lo < hi) {
+        const ull mid = (lo + hi) / 2;
+        const int c = std::memcmp(runs[i].base + mid * rec, K, kb);
+        if (c < 0 || (upper && c == 0)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Merge partitions: split vectors (one position per run) at increasing global
+// ranks 0 = r_0 < r_1 < ... < r_P = n, each partition at most cap records.
+static std::vector<std::vector<ull>> plan_partitions(const std::vector<HostRun>& runs, ull n,
+                                                     ull cap, uint32_t rec, uint32_t kb) {
+    const size_t k = runs.size();
+    const ull step = cap / (4 * k) > 0 ? cap / (4 * k) : 1;
+    struct Cand {
+        size_t run;
+        ull pos;
+        ull rank;
+    };
+    std::vector<Cand> cands;
+    for (size_t i = 0; i < k; i++)
+        for (ull p = step - 1; p < runs[i].len; p += step) cands.push_back({i, p, 0});
+    std::sort(cands.begin(), cands.end(), [&](const Cand& x, const Cand& y) {
+        const int c = std::memcmp(runs[x.run].base + x.pos * rec, runs[y.run].base + y.pos * rec, kb);
+        if (c != 0) return c < 0;
+        if (x.run != y.run) return x.run < y.run;
+        return x.pos < y.pos;
+    });
+    for (auto& c : cands) {
+        ull r = 0;
+        for (size_t i = 0; i < k; i++)
+            r += corank_split(runs, i, runs[c.run].base + c.pos * rec, c.run, c.pos, rec, kb);
+        c.rank = r;
+    }
+    std::vector<std::vector<ull>> cuts;
+    cuts.push_back(std::vector<ull>(k, 0));
+    ull start = 0;
+    const ull target = cap * 3 / 4 > 0 ? cap * 3 / 4 : 1;
+    size_t ci = 0;
+    while (n - start > cap) {
+        // the last candidate at most `target` past the current cut
+        long best = -1;
+        while (ci < cands.size() && cands[ci].rank <= start + target) {
+            if (cands[ci].rank > start) best = (long)ci;
+            ci++;
+        }
+        if (best < 0) break;  // cannot happen: consecutive ranks differ by <= cap/4
+        const Cand& c = cands[best];
+        std::vector<ull> cut(k);
+        for (size_t i = 0; i < k; i++)
+            cut[i] = corank_split(runs, i, runs[c.run].base + c.pos * rec, c.run, c.pos, rec, kb);
+        cuts.push_back(cut);
+        start = c.rank;
+    }
+    std::vector<ull> last(k);
+    for (size_t i = 0; i < k; i++) last[i] = runs[i].len;
+    cuts.push_back(last);
+    return cuts;
+}
+
+// Merge of the k sorted runs whose records lie back to back at dev_runs (run r
+// at [off[r], off[r+1]) records, off on the host): tuples, ceil(log2 k)
+// merge-path rounds, the permutation in w.perm.  Queued on st.
+static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const ull* off_host,
+                              ull* off_dev, uint32_t k, const Work& w, const Layout& L,
+                              cudaStream_t st, int sms) {
+    SortArgs m = a;
+    m.in = dev_runs;
+    m.n = off_host[k];
+    const KeySpec ks = record_keyspec(a.kb);
+    ley_status s = stage_prepare(w, L, st, m.n, 0);
+    if (s != LEY_OK) return s;
+    s = stage_extract_records(m, w, ks, st, sms, 0, 0, ceil_div_u64(m.n, kPassTile));
+    if (s != LEY_OK) return s;
+    LEY_TRY(cudaMemcpyAsync(off_dev, off_host, sizeof(ull) * (k + 1), cudaMemcpyHostToDevice, st));
+    int cur = 0;
+    for (uint32_t runs = k; runs > 1; runs = (runs + 1) / 2) {
+        LEY_TRY(launch("merge", st, [&] {
+            return launch_merge_round(st, sms * 8, w.tup[cur], w.tup[cur ^ 1], off_dev, runs,
+                                      ks.lo_mask);
+        }));
+        cur ^= 1;
+        if (runs > 2) {
+            // the merged pairs are the runs of the next round
+            LEY_TRY(launch("merge_offsets", st, [&] {
+                return launch_halve_offsets(st, off_dev, runs);
+            }));
+        }
+    }
+    LEY_TRY(launch("tuple_index", st, [&] {
+        return launch_tuple_index(st, sms * 4, w.tup[cur], w.perm, m.n);
+    }));
+    return LEY_OK;
+}
+
+// External sort (Section 3.2, Figure 1): runs of r_len records are copied in
+// on the reader stream, sorted by the internal sort and streamed into pinned
+// host scratch on the writer stream, overlapped run by run; the merge stage
+// then cuts the output into partitions by k-way co-rank, copies each
+// partition's slices of every run in, merges them by merge path, gathers the
+// records and streams them to `out`, again overlapped partition by partition.
+static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t st) {
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    const ull q = staging_records(a.n, a.rec, budget);
+    const size_t stg_bytes = align_up(q * a.rec, 256);
+    const size_t fixed = 2 * stg_bytes + 64 * 1024;
+    if (budget <= fixed) return LEY_ENOMEM;
+    // largest run (whole tiles) whose two input buffers and workspace fit
+    auto need = [&](ull r) { return 2 * align_up(r * a.rec, 256) + make_layout(r, true).total + fixed; };
+    ull lo = 0, hi = a.n / kPassTile + 1;
+    while (lo < hi) {
+        const ull mid = (lo + hi + 1) / 2;
+        if (need(mid * kPassTile) <= budget) lo = mid;
+        else hi = mid - 1;
+    }
+    const ull r_len = lo * kPassTile;
+    if (r_len == 0) return LEY_ENOMEM;
+    const uint32_t k = (uint32_t)((a.n + r_len - 1) / r_len);
+    if (k > 128) return LEY_ENOMEM;  // budget too small for the merge fan-in
+    const Layout L = make_layout(r_len, true);
+    const size_t in_bytes = align_up(r_len * a.rec, 256);
+    const size_t total = 2 * in_bytes + L.total + 2 * stg_bytes + 8 * 1024;
+    const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
+    if (dbg)
+        std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
+                     "device bytes %zu of budget %llu\n", a.n, k, r_len, q, total, budget);
+    // One external sort at a time per process: they share the host scratch.
+    std::lock_guard<std::mutex> scratch_lock(g_host_scratch_mu);
+    uint8_t* hs = host_scratch(a.n * a.rec);
+    if (!hs) return LEY_ENOMEM;
+    void* dmem = nullptr;
+    if (cudaMallocAsync(&dmem, total, st) != cudaSuccess) {
+        cudaGetLastError();
+        return LEY_ENOMEM;
+    }
+    char* base = static_cast<char*>(dmem);
+    uint8_t* dbuf[2] = {reinterpret_cast<uint8_t*>(base), reinterpret_cast<uint8_t*>(base + in_bytes)};
+    char* ws = base + 2 * in_bytes;
+    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
+                       reinterpret_cast<uint8_t*>(ws + L.total + stg_bytes)};
+    ull* off_dev = reinterpret_cast<ull*>(ws + L.total + 2 * stg_bytes);
+    ley_status s = LEY_OK;
+    {
+        HostPipe hp(st);
+        if (!hp.ok) s = LEY_ECUDA;
+        const KeySpec ks = record_keyspec(a.kb);
+        cudaEvent_t stg_free[2] = {nullptr, nullptr};
+        cudaEvent_t buf_free[2] = {nullptr, nullptr};
+        // --- run formation
+        std::vector<HostRun> runs;
+        for (uint32_t r = 0; r < k && s == LEY_OK; r++) {
+            const ull r0 = (ull)r * r_len;
+            const ull rn = a.n - r0 < r_len ? a.n - r0 : r_len;
+            const int b = r & 1;
+            if (buf_free[b] && cudaStreamWaitEvent(hp.h2d, buf_free[b], 0) != cudaSuccess) s = LEY_ECUDA;
+            SortArgs ra = a;
+            ra.in = dbuf[b];
+            ra.n = rn;
+            Work w = make_work(ws, L, rn, ds->err);
+            if (s == LEY_OK) s = stage_prepare(w, L, st, rn, 0);
+            if (s == LEY_OK) s = stream_in_extract(ra, a.in + r0 * a.rec, dbuf[b], w, ks, st, hp, ds->sms);
+            if (s == LEY_OK) s = stage_levels_finish(ra, w, ks, st, ds->sms);
+            if (s == LEY_OK) s = stream_out(ra, w.perm, 0, rn, hs + r0 * a.rec, stg, q, st, hp, stg_free, ds->sms);
+            if (s == LEY_OK) {
+                buf_free[b] = hp.ev();
+                if (!buf_free[b] || cudaEventRecord(buf_free[b], st) != cudaSuccess) s = LEY_ECUDA;
+            }
+            runs.push_back({hs + r0 * a.rec, rn});
+        }
+        // --- merge: the runs must be complete in host memory before they are cut
+        if (s == LEY_OK && cudaStreamSynchronize(hp.d2h) != cudaSuccess) s = LEY_ECUDA;
+        std::vector<std::vector<ull>> cuts;
+        if (s == LEY_OK) cuts = plan_partitions(runs, a.n, r_len, a.rec, a.kb);
+        if (dbg) std::fprintf(stderr, "leysort: runs formed (status %d), %zu merge partitions\n",
+                              (int)s, cuts.empty() ? (size_t)0 : cuts.size() - 1);
+        std::vector<ull> off_host((size_t)(k + 1) * (cuts.size() + 1));
+        ull out_pos = 0;
+        for (size_t p = 0; p + 1 < cuts.size() && s == LEY_OK; p++) {
+            const int b = p & 1;
+            ull* off = &off_host[p * (k + 1)];
+            off[0] = 0;
+            for (uint32_t i = 0; i < k; i++) off[i + 1] = off[i] + (cuts[p + 1][i] - cuts[p][i]);
+            const ull m = off[k];
+            if (m > r_len) {
+                s = LEY_ENOMEM;
+                break;
+            }
+            if (buf_free[b] && cudaStreamWaitEvent(hp.h2d, buf_free[b], 0) != cudaSuccess) s = LEY_ECUDA;
+            for (uint32_t i = 0; i < k && s == LEY_OK; i++) {
+                const ull len = cuts[p + 1][i] - cuts[p][i];
+                if (len && cudaMemcpyAsync(dbuf[b] + off[i] * a.rec, runs[i].base + cuts[p][i] * a.rec,
+                                           len * a.rec, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+                    s = LEY_ECUDA;
+            }
+            if (s == LEY_OK && !hp.order(hp.h2d, st)) s = LEY_ECUDA;
+            if (m == 0) continue;
+            Work w = make_work(ws, L, m, ds->err);
+            SortArgs ma = a;
+            ma.in = dbuf[b];
+            ma.n = m;
+            if (s == LEY_OK) s = stage_merge(ma, dbuf[b], off, off_dev, k, w, L, st, ds->sms);
+            if (s == LEY_OK) s = stream_out(ma, w.perm, 0, m, a.out + out_pos * a.rec, stg, q, st, hp, stg_free, ds->sms);
+            if (s == LEY_OK) {
+                buf_free[b] = hp.ev();
+                if (!buf_free[b] || cudaEventRecord(buf_free[b], st) != cudaSuccess) s = LEY_ECUDA;
+            }
+            out_pos += m;
+            // off_host slot p is read by the copy above; keep it until the end
+        }
+        if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
+        cudaFreeAsync(dmem, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
+    }
+    return s;
+}
+
+// Host-memory sort: partially in-memory when it fits the budget, else external.
+static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st) {
+    ley_status s = run_host_partial(a, budget, st);
+    if (s != LEY_ENOMEM || !budget) return s;
+    return run_host_external(a, budget, st);
 }
 
 // ------------------------------------------------------------- validation
@@ -387,7 +780,7 @@ ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_
         if (!aligned16(in) || !aligned16(out)) return LEY_EINVAL;
         return run_device_sort(a, mem_budget, st);
     }
-    if (ki == MK_HOST_PINNED && ko == MK_HOST_PINNED) return run_host_partial(a, mem_budget, st);
+    if (ki == MK_HOST_PINNED && ko == MK_HOST_PINNED) return run_host_sort(a, mem_budget, st);
     return LEY_EINVAL;
 }
 
@@ -445,6 +838,50 @@ ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
     a.kb = key_bytes;
     a.digit = digit;
     return run_device_sort(a, 0, st);
+}
+
+ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32_t k, void* out,
+                             uint32_t rec_bytes, uint32_t key_bytes, ley_stream_t stream) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u))
+        return LEY_EUNSUPPORTED;
+    if (k < 1 || k > 128) return LEY_EUNSUPPORTED;
+    if (!run_start) return LEY_EINVAL;
+    std::vector<ull> off(run_start, run_start + k + 1);
+    if (off[0] != 0) return LEY_EINVAL;
+    for (uint32_t i = 0; i < k; i++)
+        if (off[i + 1] < off[i]) return LEY_EINVAL;
+    const ull n = off[k];
+    if (n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+    if (n == 0) return LEY_OK;
+    if (!runs || !out) return LEY_EINVAL;
+    if (overlaps(runs, n * rec_bytes, out, n * rec_bytes)) return LEY_EINVAL;
+    if (mem_kind(runs) != MK_DEVICE || mem_kind(out) != MK_DEVICE) return LEY_EINVAL;
+    if (!aligned16(runs) || !aligned16(out)) return LEY_EINVAL;
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(n, true);
+    const size_t total = L.total + align_up(sizeof(ull) * (k + 1), 256);
+    void* base = nullptr;
+    if (cudaMallocAsync(&base, total, st) != cudaSuccess) {
+        cudaGetLastError();
+        return LEY_ENOMEM;
+    }
+    SortArgs a{};
+    a.mode = MODE_RECORDS;
+    a.in = static_cast<const uint8_t*>(runs);
+    a.out = static_cast<uint8_t*>(out);
+    a.n = n;
+    a.rec = rec_bytes;
+    a.kb = key_bytes;
+    Work w = make_work(static_cast<char*>(base), L, n, ds->err);
+    ull* off_dev = reinterpret_cast<ull*>(static_cast<char*>(base) + L.total);
+    ley_status s = stage_merge(a, a.in, off.data(), off_dev, k, w, L, st, ds->sms);
+    if (s == LEY_OK) s = stage_gather(a, w.perm, st, ds->sms, 0, n, a.out);
+    cudaFreeAsync(base, st);
+    // off is pageable host memory: its copy completed before cudaMemcpyAsync returned
+    return s;
 }
 
 ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
@@ -619,7 +1056,7 @@ static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const L
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
-    LEY_TRY(launch_gather_err(cg, a.in, a.out, w.perm, a.n, a.rec, gv, err));
+    LEY_TRY(launch_gather_err(cg, a.in, a.out, w.perm, a.n, a.n, a.rec, gv, err));
     return LEY_OK;
 }
 

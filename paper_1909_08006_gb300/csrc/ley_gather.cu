@@ -58,7 +58,7 @@ constexpr int kGatherWarps = 8;
 
 __global__ void __launch_bounds__(kGatherWarps * 32)
 k_gather100(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-            const uint32_t* __restrict__ perm, ull n, uint32_t* err) {
+            const uint32_t* __restrict__ perm, ull n, ull n_in, uint32_t* err) {
     __shared__ __align__(16) uint32_t stage[kGatherWarps][kChunk * kRecWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ull nchunks = (n + kChunk - 1) / kChunk;
@@ -71,7 +71,7 @@ k_gather100(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
         uint32_t o = 0;
         if (valid) {
             uint32_t pj = __ldg(perm + j);
-            if (pj >= n) {  // never for a valid permutation; keeps reads in bounds
+            if (pj >= n_in) {  // never for a valid permutation; keeps reads in bounds
                 LEY_FAIL(err, kErrCapacity);
                 pj = 0;
             }
@@ -172,14 +172,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // offset (record start within its window).
 __device__ __forceinline__ uint32_t tma_issue(TmaWarpBuf& wb, uint64_t* bar, int b, ull c,
                                               const uint8_t* in, const uint32_t* perm, ull n,
-                                              int lane) {
+                                              ull n_in, int lane, uint32_t* err) {
     const ull j = c * kChunk + lane;
     const ull nvalid = n - c * kChunk < (ull)kChunk ? n - c * kChunk : (ull)kChunk;
     uint32_t o = 0;
     const uint8_t* src = nullptr;
     if (j < n) {
         uint32_t pj = __ldg(perm + j);
-        if (pj >= n) pj = 0;  // never for a valid permutation; keeps reads in bounds
+        if (pj >= n_in) {  // never for a valid permutation; keeps reads in bounds
+            LEY_FAIL(err, kErrCapacity);
+            pj = 0;
+        }
         const ull s = (ull)pj * kRec;
         src = in + (s & ~15ull);
         o = (uint32_t)(s & 15) >> 2;
@@ -192,7 +195,7 @@ __device__ __forceinline__ uint32_t tma_issue(TmaWarpBuf& wb, uint64_t* bar, int
 
 __global__ void __launch_bounds__(kTmaWarps * 32)
 k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                const uint32_t* __restrict__ perm, ull n, uint32_t* err) {
+                const uint32_t* __restrict__ perm, ull n, ull n_in, uint32_t* err) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     TmaWarpBuf* bufs = reinterpret_cast<TmaWarpBuf*>(smem_raw);
     __shared__ __align__(8) uint64_t bars[kTmaWarps][kTmaBufs];
@@ -211,7 +214,7 @@ k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
     bool ok = true;
     for (int b = 0; b < kTmaBufs; b++) {
         ull c = first + b * stride;
-        if (c < nchunks) o[b] = tma_issue(wb, &bars[warp][b], b, c, in, perm, n, lane);
+        if (c < nchunks) o[b] = tma_issue(wb, &bars[warp][b], b, c, in, perm, n, n_in, lane, err);
     }
     int it = 0;
     for (ull c = first; c < nchunks; c += stride, it++) {
@@ -254,7 +257,7 @@ k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
         __syncwarp();
         // Window b is consumed: refill it with chunk c + 2*stride.
         const ull cn = c + kTmaBufs * stride;
-        if (cn < nchunks) o[b] = tma_issue(wb, &bars[warp][b], b, cn, in, perm, n, lane);
+        if (cn < nchunks) o[b] = tma_issue(wb, &bars[warp][b], b, cn, in, perm, n, n_in, lane, err);
     }
     if (!ok) {
         if (lane == 0) LEY_FAIL(err, kErrTimeout);
@@ -270,13 +273,13 @@ k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
 // Any rec_bytes that is a multiple of 4: one warp copies one record.
 __global__ void __launch_bounds__(256)
 k_gather_generic(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                 const uint32_t* __restrict__ perm, ull n, uint32_t rec) {
+                 const uint32_t* __restrict__ perm, ull n, ull n_in, uint32_t rec) {
     const int lane = threadIdx.x & 31;
     const ull warps = (ull)gridDim.x * (blockDim.x >> 5);
     const uint32_t words = rec / 4;
     for (ull j = (ull)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
         uint32_t pj = __ldg(perm + j);
-        if (pj >= n) pj = 0;  // never for a valid permutation; keeps reads in bounds
+        if (pj >= n_in) pj = 0;  // never for a valid permutation; keeps reads in bounds
         const uint32_t* s = reinterpret_cast<const uint32_t*>(in + (ull)pj * rec);
         uint32_t* d = reinterpret_cast<uint32_t*>(out + j * rec);
         for (uint32_t q = lane; q < words; q += 32) d[q] = __ldg(s + q);
@@ -303,32 +306,27 @@ int gather_blocks_per_sm(KernelKind k) {
 }
 
 extern uint32_t* device_err_word();
+cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
+                              const uint32_t* perm, ull n, ull n_in, uint32_t rec, int variant,
+                              uint32_t* err);
 
 cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
-                          const uint32_t* perm, ull n, uint32_t rec, int variant) {
-    if (rec == kRec && variant == 1) {
-        k_gather100_tma<<<c.grid, kTmaWarps * 32, tma_smem(), c.stream>>>(in, out, perm, n,
-                                                                          device_err_word());
-    } else if (rec == kRec) {
-        k_gather100<<<c.grid, kGatherWarps * 32, 0, c.stream>>>(in, out, perm, n,
-                                                                 device_err_word());
-    } else {
-        k_gather_generic<<<c.grid, 256, 0, c.stream>>>(in, out, perm, n, rec);
-    }
-    return cudaGetLastError();
+                          const uint32_t* perm, ull n, ull n_in, uint32_t rec, int variant) {
+    return launch_gather_err(c, in, out, perm, n, n_in, rec, variant, device_err_word());
 }
 
 // Same kernels as launch_gather, with the device status word given by the
 // caller instead of the library's per-device word.
 cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
-                              const uint32_t* perm, ull n, uint32_t rec, int variant,
+                              const uint32_t* perm, ull n, ull n_in, uint32_t rec, int variant,
                               uint32_t* err) {
     if (rec == kRec && variant == 1) {
-        k_gather100_tma<<<c.grid, kTmaWarps * 32, tma_smem(), c.stream>>>(in, out, perm, n, err);
+        k_gather100_tma<<<c.grid, kTmaWarps * 32, tma_smem(), c.stream>>>(in, out, perm, n, n_in,
+                                                                          err);
     } else if (rec == kRec) {
-        k_gather100<<<c.grid, kGatherWarps * 32, 0, c.stream>>>(in, out, perm, n, err);
+        k_gather100<<<c.grid, kGatherWarps * 32, 0, c.stream>>>(in, out, perm, n, n_in, err);
     } else {
-        k_gather_generic<<<c.grid, 256, 0, c.stream>>>(in, out, perm, n, rec);
+        k_gather_generic<<<c.grid, 256, 0, c.stream>>>(in, out, perm, n, n_in, rec);
     }
     return cudaGetLastError();
 }

@@ -16,6 +16,11 @@ struct LaunchCfg {
 // of the whole input (list 0, slot 0).
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, unsigned long long n,
                                    uint32_t rec_bytes, KeySpec ks, const Work& w, int hist_digit);
+// Same, for tiles [t_begin, t_end) only (kPassTile records each).
+cudaError_t launch_extract_records_tiles(const LaunchCfg& c, const uint8_t* in,
+                                         unsigned long long n, uint32_t rec_bytes, KeySpec ks,
+                                         const Work& w, int hist_digit, uint32_t t_begin,
+                                         uint32_t t_end);
 cudaError_t launch_extract_pairs(const LaunchCfg& c, const uint64_t* keys, const uint32_t* idx,
                                  unsigned long long n, KeySpec ks, const Work& w);
 cudaError_t launch_init(cudaStream_t s, const Work& w, unsigned long long n, int digit0);
@@ -27,14 +32,23 @@ cudaError_t launch_pass(const LaunchCfg& c, const Work& w, KeySpec ks, int level
 cudaError_t launch_finish_records(const LaunchCfg& c, const Work& w, KeySpec ks);
 cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, uint64_t* keys_out,
                                 uint32_t* idx_out);
+// out[j] = in[perm[j]] for j < n; perm entries are < n_in (records at `in`).
 cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
-                          const uint32_t* perm, unsigned long long n, uint32_t rec_bytes,
-                          int variant);
+                          const uint32_t* perm, unsigned long long n, unsigned long long n_in,
+                          uint32_t rec_bytes, int variant);
 cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
-                              const uint32_t* perm, unsigned long long n, uint32_t rec_bytes,
-                              int variant, uint32_t* err);
+                              const uint32_t* perm, unsigned long long n, unsigned long long n_in,
+                              uint32_t rec_bytes, int variant, uint32_t* err);
 cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsigned long long n,
                                  uint32_t* order_out, unsigned long long* hist_out);
+
+// K-way merge (ley_merge.cu): one round of pairwise merge-path merges of the
+// k sorted runs at src (run r at [off[r], off[r+1])) into dst.
+cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
+                               const unsigned long long* off_dev, uint32_t k, uint32_t lo_mask);
+cudaError_t launch_halve_offsets(cudaStream_t s, unsigned long long* off, uint32_t runs);
+cudaError_t launch_tuple_index(cudaStream_t s, int grid, const uint4* t, uint32_t* perm,
+                               unsigned long long n);
 
 // Occupancy-derived persistent grid sizes (blocks per SM) for a kernel kind.
 enum KernelKind {

@@ -1,0 +1,138 @@
+// K-way merge of sorted runs (the merge stage of Section 3.2: "sorted and
+// merged by the merger thread to a globally sorted partition, using a K-way
+// merge algorithm"), done on the GPU as rounds of pairwise merge-path merges
+// (Green, McColl and Bader, "GPU Merge Path", 2012) over 16-byte tuples.
+//
+// The k runs lie back to back in one tuple array, run r at [off[r], off[r+1]),
+// each sorted by (key, position).  Positions grow with the run number, so
+// comparing full tuples (key, then position) merges stably: on equal keys the
+// lower run comes first, which is the order of the input.  Round by round,
+// runs 2i and 2i+1 are merged into the other buffer at the same place; an odd
+// last run is copied.  ceil(log2 k) rounds sort the whole array.
+#define LEY_FILE_ID 3
+#include "ley_kernels.h"
+
+namespace ley {
+
+using ull = unsigned long long;
+
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 4;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;   // 1024 outputs per tile
+
+__device__ __forceinline__ bool mtup_less(const uint4& a, const uint4& b, uint32_t lo_mask) {
+    const ull ka = ((ull)a.y << 32) | a.x, kb = ((ull)b.y << 32) | b.x;
+    if (ka != kb) return ka < kb;
+    const uint32_t la = a.z & lo_mask, lb = b.z & lo_mask;
+    if (la != lb) return la < lb;
+    return a.w < b.w;
+}
+
+// Number of A elements among the first d outputs of the stable merge of
+// A[0, na) and B[0, nb) (A first on ties): the merge-path split of diagonal d.
+template <class GetA, class GetB>
+__device__ __forceinline__ uint32_t merge_split(uint32_t d, uint32_t na, uint32_t nb,
+                                                GetA geta, GetB getb, uint32_t lo_mask) {
+    uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        // A[mid] is among the first d outputs iff it precedes B[d - 1 - mid]
+        if (mtup_less(geta(mid), getb(d - 1 - mid), lo_mask)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One merge round.  pair p merges runs 2p and 2p+1 of `off` (k runs); its
+// output [off[2p], off[min(2p+2, k)]) is cut into tiles of kMergeTile, and
+// the tiles of all pairs are numbered consecutively.
+__global__ void __launch_bounds__(kMergeThreads)
+k_merge_round(const uint4* __restrict__ src, uint4* __restrict__ dst, const ull* __restrict__ off,
+              uint32_t k, uint32_t lo_mask) {
+    __shared__ uint4 sa[kMergeTile];
+    __shared__ uint4 so[kMergeTile];
+    __shared__ uint32_t tile_base[65];
+    const uint32_t npairs = (k + 1) / 2;
+    if (threadIdx.x == 0) {
+        uint32_t tb = 0;
+        for (uint32_t p = 0; p < npairs && p < 64; p++) {
+            tile_base[p] = tb;
+            const ull len = off[min(2 * p + 2, k)] - off[2 * p];
+            tb += (uint32_t)((len + kMergeTile - 1) / kMergeTile);
+        }
+        tile_base[min(npairs, 64u)] = tb;
+    }
+    __syncthreads();
+    const uint32_t ntiles = tile_base[min(npairs, 64u)];
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t p = 0;
+        while (p + 1 < npairs && tile_base[p + 1] <= t) p++;
+        const ull a0 = off[2 * p];
+        const ull a1 = off[min(2 * p + 1, k)];
+        const ull b1 = off[min(2 * p + 2, k)];
+        const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - a1);
+        const uint32_t d0 = (t - tile_base[p]) * kMergeTile;
+        const uint32_t d1 = min(d0 + kMergeTile, na + nb);
+        const uint4* A = src + a0;
+        const uint4* Bv = src + a1;
+        auto ga = [&](uint32_t i) { return A[i]; };
+        auto gb = [&](uint32_t i) { return Bv[i]; };
+        const uint32_t s0 = merge_split(d0, na, nb, ga, gb, lo_mask);
+        const uint32_t s1 = merge_split(d1, na, nb, ga, gb, lo_mask);
+        // stage A[s0, s1) then B[d0 - s0, d1 - s1) in shared memory
+        const uint32_t ca = s1 - s0, cb = (d1 - s1) - (d0 - s0), m = ca + cb;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += kMergeThreads)
+            sa[i] = i < ca ? A[s0 + i] : Bv[d0 - s0 + (i - ca)];
+        __syncthreads();
+        // each thread merges kMergeItems consecutive outputs of the tile
+        const uint32_t my0 = min(threadIdx.x * kMergeItems, m);
+        const uint32_t my1 = min(my0 + kMergeItems, m);
+        auto la = [&](uint32_t i) { return sa[i]; };
+        auto lb = [&](uint32_t i) { return sa[ca + i]; };
+        uint32_t ia = merge_split(my0, ca, cb, la, lb, lo_mask);
+        uint32_t ib = my0 - ia;
+        for (uint32_t o = my0; o < my1; o++) {
+            bool take_a;
+            if (ia >= ca) take_a = false;
+            else if (ib >= cb) take_a = true;
+            else take_a = !mtup_less(sa[ca + ib], sa[ia], lo_mask);
+            so[o] = take_a ? sa[ia++] : sa[ca + ib++];
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += kMergeThreads) dst[a0 + d0 + i] = so[i];
+    }
+}
+
+cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
+                               const ull* off_dev, uint32_t k, uint32_t lo_mask) {
+    k_merge_round<<<grid, kMergeThreads, 0, s>>>(src, dst, off_dev, k, lo_mask);
+    return cudaGetLastError();
+}
+
+// After a round over `runs` runs, the merged pairs are the next round's runs:
+// off'[i] = off[min(2i, runs)] for i = 0 .. ceil(runs / 2).  In place: entry
+// i is written after every read of entries < 2i.
+__global__ void k_halve_offsets(ull* off, uint32_t runs) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t np = (runs + 1) / 2;
+    for (uint32_t i = 1; i <= np; i++) off[i] = off[min(2 * i, runs)];
+}
+
+cudaError_t launch_halve_offsets(cudaStream_t s, ull* off, uint32_t runs) {
+    k_halve_offsets<<<1, 32, 0, s>>>(off, runs);
+    return cudaGetLastError();
+}
+
+// Copies the tuples' input positions (the w field) out as the permutation.
+__global__ void k_tuple_index(const uint4* __restrict__ t, uint32_t* __restrict__ perm, ull n) {
+    for (ull i = (ull)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (ull)gridDim.x * blockDim.x)
+        perm[i] = t[i].w;
+}
+
+cudaError_t launch_tuple_index(cudaStream_t s, int grid, const uint4* t, uint32_t* perm, ull n) {
+    k_tuple_index<<<grid, 256, 0, s>>>(t, perm, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ley

@@ -177,7 +177,7 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool v
 template <int REC>
 __global__ void __launch_bounds__(256)
 k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpec ks, Work w,
-                  int hist_digit) {
+                  int hist_digit, uint32_t t_begin, uint32_t t_end) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
     if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
@@ -188,8 +188,7 @@ k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpe
     ull dhi = 0;
     uint32_t dlo = 0;
     constexpr int U = 4;
-    const uint32_t ntiles = ceil_div_u64(n, kPassTile);
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (uint32_t t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
         __syncthreads();
         sh_hist[threadIdx.x] = 0;
         __syncthreads();
@@ -1229,10 +1228,21 @@ namespace ley {
 
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, ull n, uint32_t rec,
                                    KeySpec ks, const Work& w, int hist_digit) {
+    return launch_extract_records_tiles(c, in, n, rec, ks, w, hist_digit, 0,
+                                        ceil_div_u64(n, kPassTile));
+}
+
+cudaError_t launch_extract_records_tiles(const LaunchCfg& c, const uint8_t* in, ull n,
+                                         uint32_t rec, KeySpec ks, const Work& w, int hist_digit,
+                                         uint32_t t_begin, uint32_t t_end) {
+    if (t_end <= t_begin) return cudaSuccess;
+    const int grid = (int)min((uint32_t)c.grid, t_end - t_begin);
     if (rec == 100)
-        k_extract_records<100><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit);
+        k_extract_records<100><<<grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit, t_begin,
+                                                           t_end);
     else
-        k_extract_records<0><<<c.grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit);
+        k_extract_records<0><<<grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit, t_begin,
+                                                         t_end);
     return cudaGetLastError();
 }
 
