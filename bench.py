@@ -57,25 +57,22 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def source_hash() -> str:
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1909_08006_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+def source_hash(name: str) -> str:
+    """Hash of one CUDA source file of the library."""
+    with open(os.path.join(ROOT, "paper_1909_08006_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def committed_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current source of that kernel's file; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(e.get("source_file", "")):
         return None
     return e.get("bytes_per_launch")
 
@@ -162,12 +159,13 @@ def barrier(pg, device=None):
 
 # ----------------------------------------------------------- CPU baseline
 
-def oracle_sample(n_sample: int, seed: int = 2):
+def oracle_sample(n_sample: int, seed: int = 2, skew: bool = False, device=None):
     """The CPU oracle (single-threaded qsort on (key, index) + record copy) on
     the first n_sample records of the workload.  Returns (GB/s, seconds)."""
     import datagen
     import oracle
-    recs = datagen.uniform_records(n_sample, seed=seed).numpy()
+    gen = datagen.skew_records if skew else datagen.uniform_records
+    recs = gen(n_sample, seed=seed, device=device or "cpu").cpu().numpy()
     oracle.build()
     t0 = time.perf_counter()
     oracle.sort_records(recs, key_bytes=KEY)
@@ -186,7 +184,13 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(dev)
     n = args.n
     stream = torch.cuda.Stream(dev)
-    d_in = datagen.uniform_records(n, seed=2, device=dev)
+    wl = args.workload
+    if wl == "pairs":
+        return run_pairs(args, world, rank, dev, stream, pg)
+    if wl in ("partial", "external"):
+        return run_host_mode(args, world, rank, dev, stream, pg)
+    gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
+    d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
     d_out = torch.empty_like(d_in)
     torch.cuda.synchronize()
 
@@ -243,7 +247,7 @@ def run_ours(args, world, rank, local, pg):
     # the dominant kernel moves its bytes in one launch (gather) or in the
     # launches that carry work (pass: two levels at uniform keys)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    workload = f"uniform_{n}"
+    workload = f"{wl}_{n}"
     roofline = {
         "kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
@@ -273,14 +277,15 @@ def run_ours(args, world, rank, local, pg):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = oracle_sample(args.cpu_sample)
+        v, dt = oracle_sample(args.cpu_sample, seed=2 if wl == "uniform" else 3,
+                              skew=wl == "skew", device=dev)
         cpu = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {args.cpu_sample} records of the workload, "
                          f"single-threaded qsort + record copy, {dt:.1f} s"}
 
     value = world * n * REC / (ms * 1e-3) / 1e9
     return {
-        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "metric": METRIC if wl == "uniform" else f"GB/s of 100-byte records sorted ({wl} keys)", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded SplitMix64 records shaped like the paper's gensort data)",
@@ -289,6 +294,101 @@ def run_ours(args, world, rank, local, pg):
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
         "cpu_baseline": cpu, "kernels": kernels,
+    }
+
+
+# ------------------------------------------------------ other workloads
+
+def _timed(fn, steps, warmup, stream, pg, dev):
+    import torch
+    for _ in range(warmup):
+        fn()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1) / steps, pg, dev)
+
+
+def run_pairs(args, world, rank, dev, stream, pg):
+    """Key-pointer pairs (u64 key, u32 index): the sort without record gather."""
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    n = args.n
+    keys, idx = datagen.uniform_pairs(n, seed=5, device=dev)
+    ko, io = torch.empty_like(keys), torch.empty_like(idx)
+    torch.cuda.synchronize()
+    step = lambda: ley.ley_sort_keys_index(keys, idx, ko, io, stream=stream)  # noqa: E731
+    launches0 = ley.ley_launch_count()
+    ms = _timed(step, args.steps, args.warmup, stream, pg, dev)
+    launches = (ley.ley_launch_count() - launches0) * args.steps // (args.steps + args.warmup)
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error")
+    return {
+        "metric": "pairs sorted per second (u64 key, u32 index)",
+        "value": round(world * n / (ms * 1e-3) / 1e9, 4), "unit": "Gpairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "gpu_launches": launches,
+        "config": {"workload": f"pairs_{n}", "pairs": n, "bytes_per_pair": 12},
+    }
+
+
+def run_host_mode(args, world, rank, dev, stream, pg):
+    """Records in pinned host memory, sorted to pinned host memory under a
+    device budget: the partially in-memory sort (input resident on the device)
+    or the external sort (runs + k-way merge)."""
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    import numpy as np
+    n, budget = args.n, int(args.budget_gb * 1e9)
+    cudart = torch.cuda.cudart()
+
+    def pinned(nbytes):
+        # exact-size page-locked buffer (torch's pinned pool rounds up to 2^k)
+        a = np.empty(nbytes, dtype=np.uint8)
+        rc = cudart.cudaHostRegister(a.ctypes.data, nbytes, 0)
+        if int(rc) != 0:
+            raise RuntimeError(f"cudaHostRegister failed ({rc})")
+        return a
+
+    h_in_np, h_out_np = pinned(n * REC), pinned(n * REC)
+    h_in = torch.from_numpy(h_in_np).view(n, REC)
+    h_out = torch.from_numpy(h_out_np).view(n, REC)
+    chunk = 50_000_000
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        h_in[c0:c1].copy_(datagen.uniform_records(c1 - c0, seed=2, device=dev, start=c0).cpu())
+    steps, warm = max(1, args.steps), max(1, min(args.warmup, 1))
+    for _ in range(warm):
+        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, mem_budget=budget,
+                             stream=stream)
+    barrier(pg, dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, mem_budget=budget,
+                             stream=stream)
+    dt = max_over_ranks((time.perf_counter() - t0) / steps, pg, dev)
+    ws = ley.ley_workspace_bytes(n)
+    mode = "partial" if n * REC + ws <= budget else "external"
+    for a in (h_in_np, h_out_np):
+        cudart.cudaHostUnregister(a.ctypes.data)
+    link = 2 * n * REC if mode == "partial" else 4 * n * REC
+    return {
+        "metric": f"GB/s of 100-byte records sorted host-to-host ({mode}, device budget)",
+        "value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": round(dt * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": f"{args.workload}_{n}", "records": n,
+                                        "budget_bytes": budget, "mode": mode,
+                                        "link_bytes_per_step": link},
+        "link_GBps": round(link / dt / 1e9, 2),
     }
 
 
@@ -337,10 +437,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=2_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=20_000_000)
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "skew", "pairs", "partial", "external"])
+    ap.add_argument("--budget-gb", type=float, default=30.0)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "external" and args.n == 100_000_000:
+        args.n = 400_000_000
+    if args.workload == "partial" and args.n == 100_000_000:
+        args.n = 200_000_000
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         out = run_reference(args, world, rank, pg)
