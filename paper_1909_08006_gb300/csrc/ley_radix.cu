@@ -571,20 +571,66 @@ k_classify(Work w, KeySpec ks, int L) {
         }
         const int nb = sg.buf ^ 1;
         const int d1 = sg.digit + 1;
-        // Big sub-buckets recurse: the warp appends them one by one.
+        // Big sub-buckets recurse.  The warp reserves list slots and tiles for
+        // all of them with one atomic (slot and tile order agree), then each
+        // lane writes its own bins' entries and tile owners.
+        uint32_t nbig = 0, tbig = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            uint32_t big = __ballot_sync(0xffffffffu, c8[k] > (uint32_t)kSmall);
-            while (big) {
-                const int src = __ffs(big) - 1;
-                big &= big - 1;
-                const uint32_t c = __shfl_sync(0xffffffffu, c8[k], src);
-                const uint32_t o = __shfl_sync(0xffffffffu, off8[k], src);
-                if (d1 < ks.ndig)
-                    append_big_warp(w, L + 1, sg.start + o, c, d1, nb);
-                else if (lane == 0)
-                    emit_fin(w, sg.start + o, c, ks.ndig, nb, 1);
+        for (int k = 0; k < 8; k++)
+            if (c8[k] > (uint32_t)kSmall) {
+                nbig++;
+                tbig += ceil_div_u64(c8[k], kPassTile);
             }
+        if (d1 < ks.ndig) {
+            uint32_t nb_incl = nbig, tb_incl = tbig;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y1 = __shfl_up_sync(0xffffffffu, nb_incl, o);
+                const uint32_t y2 = __shfl_up_sync(0xffffffffu, tb_incl, o);
+                if (lane >= o) {
+                    nb_incl += y1;
+                    tb_incl += y2;
+                }
+            }
+            const uint32_t nb_tot = __shfl_sync(0xffffffffu, nb_incl, 31);
+            const uint32_t tb_tot = __shfl_sync(0xffffffffu, tb_incl, 31);
+            ull pk0 = 0;
+            if (lane == 0 && nb_tot)
+                pk0 = atomicAdd(&w.ctl->lvl[L + 1].big_packed,
+                                ((ull)nb_tot << kPackShift) | (ull)tb_tot);
+            pk0 = __shfl_sync(0xffffffffu, pk0, 0);
+            ull slot = (pk0 >> kPackShift) + (nb_incl - nbig);
+            ull tile = (pk0 & kPackMask) + (tb_incl - tbig);
+            const int q = (L + 1) & 1;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (c8[k] <= (uint32_t)kSmall) continue;
+                const uint32_t nt = ceil_div_u64(c8[k], kPassTile);
+                if (slot >= w.cap_seg || tile + nt > w.cap_tiles) {
+                    LEY_FAIL(w.err, kErrCapacity);
+                    break;
+                }
+                Seg sgn;
+                sgn.start = sg.start + off8[k];
+                sgn.count = c8[k];
+                sgn.digit = (uint16_t)d1;
+                sgn.buf = (uint8_t)nb;
+                sgn.pad = 0;
+                w.segs[q][slot] = sgn;
+                w.seg_tile_base[q][slot] = (uint32_t)tile;
+                Diff z;
+                z.hi = 0;
+                z.lo = 0;
+                z.pad = 0;
+                w.diff[q][slot] = z;
+                for (uint32_t i = 0; i < nt; i++) w.seg_tile_owner[q][tile + i] = (uint32_t)slot;
+                slot++;
+                tile += nt;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                if (c8[k] > (uint32_t)kSmall) emit_fin(w, sg.start + off8[k], c8[k], ks.ndig, nb, 1);
         }
         // Runs of small sub-buckets are packed greedily into finishing tasks
         // (lane 0 walks the bins in shared memory, the warp then reserves all
@@ -865,7 +911,9 @@ __device__ __forceinline__ void stack_push(FinShared& S, uint32_t s, uint32_t c,
 // Block-wide stable counting pass on B[r0, r0+c) -- or, with FROM_GLOBAL,
 // on the c tuples at gsrc, staged into B[r0, r0+c) -- from digit d0 on
 // (SingleThreadRadixSort of Algorithm 1, one CTA instead of one thread).
-// Its sub-buckets are finished here by comparison ranking when tiny, else
+// Digit d0 is tried first; only when it is the same for every tuple is the
+// key-difference mask reduced to find the first digit where keys differ.
+// Sub-buckets are finished here by comparison ranking when tiny, else
 // queued for a warp (<= kWarpMax) or pushed for the whole CTA.
 template <bool FROM_GLOBAL>
 __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0,
@@ -874,9 +922,6 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
     const uint32_t lt_mask = lanemask_lt();
     uint4 v[kFinItems];
     uint32_t rd[kFinItems];
-    if (tid < 3) S.d3[tid] = 0;
-#pragma unroll
-    for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
     const uint4 ref = FROM_GLOBAL ? gsrc[0] : B[r0];
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
@@ -886,64 +931,77 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         else
             v[k] = idx < c ? B[r0 + idx] : ref;
     }
-    ull dhi = 0;
-    uint32_t dlo = 0;
+    int ds = d0 < ks.ndig ? d0 : ks.ndig - 1;
+    for (int attempt = 0;; attempt++) {
 #pragma unroll
-    for (int k = 0; k < kFinItems; k++) {
-        dhi |= key_hi(v[k]) ^ key_hi(ref);
-        dlo |= v[k].z ^ ref.z;
-    }
-    __syncthreads();  // counters zeroed, all reads of B done
+        for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
+        __syncthreads();  // counters zeroed (and, first time, all reads of B done)
 #ifdef LEY_PHASE_TIMING
-    if (FROM_GLOBAL && threadIdx.x == 0) atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
+        if (FROM_GLOBAL && attempt == 0 && threadIdx.x == 0)
+            atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
 #endif
-    warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, S.d3);
-    __syncthreads();
-    const int ds = first_varying_digit(((ull)S.d3[0] << 32) | S.d3[1], S.d3[2], d0, ks.ndig);
-    if (ds >= ks.ndig) {
-        // All keys equal: the input order is the answer.
 #pragma unroll
         for (int k = 0; k < kFinItems; k++) {
             const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
-            if (idx < c) {
-                if (FROM_GLOBAL) B[r0 + idx] = v[k];
-                S.order[r0 + idx] = (uint16_t)(r0 + idx);
-            }
+            const bool valid = idx < c;
+            const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
+            rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
         }
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < kFinItems; k++) {
-        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
-        const bool valid = idx < c;
-        const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
-        rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
-    }
-    __syncthreads();
-    {
-        const int dig = tid;
-        uint32_t run = 0;
-#pragma unroll
-        for (int ww = 0; ww < kFinWarps; ww++) {
-            const uint32_t cc = S.cnt[ww][dig];
-            S.cnt[ww][dig] = run;
-            run += cc;
-        }
-        uint32_t incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) S.warp_tot[warp] = incl;
         __syncthreads();
-        uint32_t wp = 0;
+        {
+            const int dig = tid;
+            uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < kFinWarps; ww++) wp += ww < warp ? S.warp_tot[ww] : 0u;
-        S.sb_off[dig] = (uint16_t)(wp + incl - run);
-        S.sb_cnt[dig] = (uint16_t)run;
+            for (int ww = 0; ww < kFinWarps; ww++) {
+                const uint32_t cc = S.cnt[ww][dig];
+                S.cnt[ww][dig] = run;
+                run += cc;
+            }
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) S.warp_tot[warp] = incl;
+            __syncthreads();
+            uint32_t wp = 0;
+#pragma unroll
+            for (int ww = 0; ww < kFinWarps; ww++) wp += ww < warp ? S.warp_tot[ww] : 0u;
+            S.sb_off[dig] = (uint16_t)(wp + incl - run);
+            S.sb_cnt[dig] = (uint16_t)run;
+        }
+        __syncthreads();
+        if (S.sb_cnt[digit_of(ref, ds)] != c) break;  // digit ds splits the range
+        // Digit ds is the same for every tuple: find where the keys differ.
+        if (tid < 3) S.d3[tid] = 0;
+        ull dhi = 0;
+        uint32_t dlo = 0;
+#pragma unroll
+        for (int k = 0; k < kFinItems; k++) {
+            dhi |= key_hi(v[k]) ^ key_hi(ref);
+            dlo |= v[k].z ^ ref.z;
+        }
+        __syncthreads();
+        warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, S.d3);
+        __syncthreads();
+        const int d2 = first_varying_digit(((ull)S.d3[0] << 32) | S.d3[1], S.d3[2], ds + 1,
+                                           ks.ndig);
+        if (d2 >= ks.ndig) {
+            // All keys equal: the input order is the answer.
+#pragma unroll
+            for (int k = 0; k < kFinItems; k++) {
+                const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+                if (idx < c) {
+                    if (FROM_GLOBAL) B[r0 + idx] = v[k];
+                    S.order[r0 + idx] = (uint16_t)(r0 + idx);
+                }
+            }
+            return;
+        }
+        ds = d2;
+        __syncthreads();  // everyone has read sb_cnt and d3 before the next attempt
     }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
         const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
@@ -1135,73 +1193,72 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
+    if (tid == 0) S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
     LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
         LEY_PHASE(10);
-        if (tid == 0) {
-            S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
-            S.q_head = S.q_tail = S.q_pending = S.bs_n = 0;
-        }
-        __syncthreads();
         const uint32_t ti = S.task;
         if (ti >= nfin) break;
-        LEY_PHASE(11);
         const FinTask tk = w.fin[ti];
-        if (tk.start + tk.count > w.n || tk.buf > 1) {  // never for a valid task list
-            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
-            continue;
+        __syncthreads();  // every thread has read S.task
+        // Claim the next task now; its number is needed only at the end.
+        uint32_t next = 0;
+        if (tid == 0) {
+            next = atomicAdd(&w.ctl->fin_ctr, 1u);
+            S.q_head = S.q_tail = S.q_pending = S.bs_n = 0;
         }
-        const uint4* src = w.tup[tk.buf] + tk.start;
-        if (tk.flags & 1) {  // all keys equal: input order
+        LEY_PHASE(11);
+        bool skip = false;
+        if (tk.start + tk.count > w.n || tk.buf > 1 ||
+            (!(tk.flags & 1) && tk.count > (uint32_t)kSmall)) {  // never for a valid task list
+            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
+            skip = true;
+        }
+        const uint4* src = w.tup[tk.buf & 1] + tk.start;
+        if (!skip && (tk.flags & 1)) {  // all keys equal: input order
             for (uint32_t i = tid; i < tk.count; i += kFinThreads) emit(tk.start + i, src[i]);
-            continue;
+            skip = true;
         }
-        if (tk.count > (uint32_t)kSmall) {  // never produced by k_classify
-            if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
-            continue;
-        }
-        fin_block_pass<true>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
-        __syncthreads();
-        LEY_PHASE(12);
-        while (true) {
+        if (!skip) {
+            fin_block_pass<true>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
             __syncthreads();
-            fin_drain_queue(B, S, ks, w.err);
-            __syncthreads();
-            const int ns = S.bs_n;
-            if (ns <= 0) break;
-            const int top = (ns > kFinStack ? kFinStack : ns) - 1;
-            const uint32_t meta = S.bs_meta[top];
-            const int dg = S.bs_dig[top];
-            __syncthreads();
-            if (tid == 0) S.bs_n = top;
-            if ((meta & 0xFFFFu) + (meta >> 16) > (uint32_t)kSmall) {
-                if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
-                continue;
-            }
-            fin_block_pass<false>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
-        }
-        LEY_PHASE(13);
-        // Coalesced write of the task's final order.
-        for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
-            uint32_t o = S.order[j];
-            if (o >= tk.count) {  // a position left unset: report, stay in bounds
-                LEY_FAIL(w.err, kErrCapacity);
-#ifdef LEY_PHASE_TIMING
-                if (atomicCAS(&g_ley_phase[40], 0ull, 1ull) == 0ull) {
-                    g_ley_phase[41] = tk.start;
-                    g_ley_phase[42] = tk.count;
-                    g_ley_phase[43] = tk.digit | (tk.flags << 8) | (tk.buf << 16);
-                    g_ley_phase[44] = j;
-                    g_ley_phase[45] = o;
-                    g_ley_phase[46] = ti;
+            LEY_PHASE(12);
+            while (S.q_tail != 0 || S.bs_n != 0) {
+                fin_drain_queue(B, S, ks, w.err);
+                __syncthreads();
+                const int ns = S.bs_n;
+                if (ns <= 0) break;
+                const int top = (ns > kFinStack ? kFinStack : ns) - 1;
+                const uint32_t meta = S.bs_meta[top];
+                const int dg = S.bs_dig[top];
+                __syncthreads();
+                if (tid == 0) {
+                    S.bs_n = top;
+                    S.q_head = S.q_tail = S.q_pending = 0;
                 }
-#endif
-                o = 0;
+                if ((meta & 0xFFFFu) + (meta >> 16) > (uint32_t)kSmall) {
+                    if (tid == 0) LEY_FAIL(w.err, kErrCapacity);
+                    __syncthreads();
+                    continue;
+                }
+                fin_block_pass<false>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
+                __syncthreads();
             }
-            emit(tk.start + j, B[o]);
+            LEY_PHASE(13);
+            // Coalesced write of the task's final order.
+            for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
+                uint32_t o = S.order[j];
+                if (o >= tk.count) {  // a position left unset: report, stay in bounds
+                    LEY_FAIL(w.err, kErrCapacity);
+                    o = 0;
+                }
+                emit(tk.start + j, B[o]);
+            }
+            LEY_PHASE(14);
         }
-        LEY_PHASE(14);
+        __syncthreads();
+        if (tid == 0) S.task = next;
     }
 }
 
