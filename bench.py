@@ -44,8 +44,10 @@ ALG_BYTES = {
     "hist": 16,           # tuple in
     "finish": 16 + 4,     # tuple in, u32 permutation out
     "gather": 4 + 100 + 100,  # permutation + record in, record out
+    # finishing with the record gather fused in: tuple in, record in, record out
+    "finish_gather": 16 + 100 + 100,
 }
-PATH_BYTES = 314          # whole path: extract + 2 passes + finish + gather
+PATH_BYTES = 306          # whole path: extract + 2 passes + finish with the gather
 
 
 def load_peaks():

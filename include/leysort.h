@@ -26,6 +26,12 @@
  *  - Errors found on the host are returned before any work is queued.  Errors
  *    found by a kernel (a bounded wait that gave up) are latched in a
  *    per-device status word read by ley_last_device_status().
+ *  - The first call on a device sets that device's current context's L2
+ *    fetch granularity limit (cudaLimitMaxL2FetchGranularity) to 32 bytes,
+ *    because the key reads and record gathers touch scattered 32-byte
+ *    sectors.  The limit is a performance hint of the caller's context and
+ *    ends with it; the environment variable LEY_L2_FETCH_BYTES=<0..128> picks
+ *    another value and LEY_L2_FETCH_BYTES=keep leaves the context's own.
  */
 #ifndef LEYSORT_H
 #define LEYSORT_H

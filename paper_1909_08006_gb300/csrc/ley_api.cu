@@ -27,6 +27,25 @@ static DevState g_dev[64];
 static std::mutex g_mu;
 static std::atomic<unsigned long long> g_launches{0};
 
+// The record path reads 10..12-byte keys out of 100-byte records (extract)
+// and 100-byte records at random positions (gather); at the context's
+// default L2 fetch granularity each such read brings whole 64- or 128-byte
+// lines in from HBM.  A 32-byte granularity fetches only the touched sectors
+// (measured on GB300 at 1e8 records: extract 1.65 -> 0.98 ms, gather 5.03 ->
+// 4.61 ms).  The limit is a per-context performance hint that ends with the
+// context; LEY_L2_FETCH_BYTES=<0..128> picks another value, "keep" leaves the
+// context's own.
+static void set_l2_fetch_granularity() {
+    size_t bytes = 32;
+    if (const char* e = getenv("LEY_L2_FETCH_BYTES")) {
+        if (strcmp(e, "keep") == 0) return;
+        bytes = (size_t)strtoul(e, nullptr, 10);
+        if (bytes > 128) bytes = 128;
+    }
+    if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, bytes) != cudaSuccess)
+        (void)cudaGetLastError();  // a hint: an unsupported value changes nothing
+}
+
 static DevState* dev_state() {
     int d = 0;
     if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
@@ -40,6 +59,7 @@ static DevState* dev_state() {
         if (cudaMemset(p, 0, 256) != cudaSuccess) return nullptr;
         s.err = static_cast<uint32_t*>(p);
         (void)blocks_per_sm(KK_PASS);  // occupancy tables and smem attributes
+        set_l2_fetch_granularity();
         s.init = true;
     }
     return &s;
@@ -193,13 +213,20 @@ static KeySpec pair_keyspec() {
     return ks;
 }
 
-// Record gather kernel: TMA bulk copies (default) or plain vector loads
-// (LEY_GATHER=lsu), kept for comparison.
+// Record gather for 100-byte records: by default the internal sort gathers
+// the records inside the finishing kernel (2); the separate gather kernel
+// with TMA bulk copies (1, LEY_GATHER=tma) serves the chunked host-memory
+// modes; plain vector loads (0, LEY_GATHER=lsu) are kept for comparison.
 static int gather_variant() {
     const char* v = std::getenv("LEY_GATHER");
     if (v && std::strcmp(v, "lsu") == 0) return 0;
-    return 1;
+    if (v && std::strcmp(v, "tma") == 0) return 1;
+    return 2;
 }
+
+// Whether an internal sort of this geometry fuses the gather into the finish
+// (and so needs no permutation array).
+static bool fused_gather(uint32_t rec) { return rec == 100 && gather_variant() == 2; }
 
 // ----------------------------------------------------- the internal sort
 
@@ -249,7 +276,7 @@ static ley_status stage_extract_records(const SortArgs& a, const Work& w, const 
 // The MSD levels (histogram, offset scan, classify, scatter) and the
 // small-bucket finish; records mode leaves the permutation in w.perm.
 static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const KeySpec& ks,
-                                      cudaStream_t st, int sms) {
+                                      cudaStream_t st, int sms, bool fuse = false) {
     const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
@@ -268,6 +295,14 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
         }));
         return LEY_OK;
     }
+    if (fuse) {  // records gathered into a.out by the finishing kernel itself
+        LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_GATHER), kFinThreads,
+                     kernel_smem(KK_FINISH_GATHER), st};
+        LEY_TRY(launch("finish_gather", st, [&] {
+            return launch_finish_gather(cf, w, ks, a.in, a.out, a.n);
+        }));
+        return LEY_OK;
+    }
     LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
     LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
     return LEY_OK;
@@ -277,7 +312,7 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
 static ley_status stage_gather(const SortArgs& a, const uint32_t* perm, cudaStream_t st, int sms,
                                ull j0, ull j1, uint8_t* out_base) {
     if (j1 <= j0) return LEY_OK;
-    const int gv = a.rec == 100 ? gather_variant() : 0;
+    const int gv = a.rec == 100 ? (gather_variant() == 0 ? 0 : 1) : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
@@ -316,15 +351,16 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
         }));
         return LEY_OK;
     }
-    s = stage_levels_finish(a, w, ks, st, sms);
-    if (s != LEY_OK || a.mode == MODE_PAIRS) return s;
+    const bool fuse = a.mode == MODE_RECORDS && fused_gather(a.rec);
+    s = stage_levels_finish(a, w, ks, st, sms, fuse);
+    if (s != LEY_OK || a.mode == MODE_PAIRS || fuse) return s;
     return stage_gather(a, w.perm, st, sms, 0, a.n, a.out);
 }
 
 static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
-    const Layout L = make_layout(a.n, a.mode == MODE_RECORDS);
+    const Layout L = make_layout(a.n, a.mode == MODE_RECORDS && !fused_gather(a.rec));
     if (budget && L.total > budget) return LEY_ENOMEM;
     void* base = nullptr;
     if (cudaMallocAsync(&base, L.total, st) != cudaSuccess) {
@@ -890,7 +926,7 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
     if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
         rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
-    *bytes = n ? make_layout(n, true).total : 0;
+    *bytes = n ? make_layout(n, !fused_gather(rec_bytes)).total : 0;
     return LEY_OK;
 }
 
@@ -1052,7 +1088,7 @@ static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const L
     }
     LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
     LEY_TRY(launch_finish_records(cf, w, ks));
-    const int gv = a.rec == 100 ? gather_variant() : 0;
+    const int gv = a.rec == 100 ? (gather_variant() == 0 ? 0 : 1) : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};

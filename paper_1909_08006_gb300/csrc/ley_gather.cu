@@ -11,39 +11,15 @@
 // leaves a 16-byte granule that holds record bytes.
 #define LEY_FILE_ID 2
 #include "ley_kernels.h"
+#include "ley_rec100.cuh"
 #include "ley_tma.cuh"
 
 namespace ley {
 
 using ull = unsigned long long;
 
-constexpr int kRec = 100;
-constexpr int kRecWords = kRec / 4;            // 25
-constexpr int kWinBytes = 112;                 // 7 x 16 B
 constexpr int kChunk = 32;                     // records per warp tile
 constexpr int kChunkBytes = kChunk * kRec;     // 3200
-
-// Copy words o..o+24 of a 28-word window into the staging tile.
-__device__ __forceinline__ void shift_store(uint32_t* st, const uint32_t (&w)[28], uint32_t o) {
-    switch (o) {
-        case 0:
-#pragma unroll
-            for (int k = 0; k < kRecWords; k++) st[k] = w[k];
-            break;
-        case 1:
-#pragma unroll
-            for (int k = 0; k < kRecWords; k++) st[k] = w[k + 1];
-            break;
-        case 2:
-#pragma unroll
-            for (int k = 0; k < kRecWords; k++) st[k] = w[k + 2];
-            break;
-        default:
-#pragma unroll
-            for (int k = 0; k < kRecWords; k++) st[k] = w[k + 3];
-            break;
-    }
-}
 
 __device__ __forceinline__ uint4 ldg_nc_na(const uint4* p) {
     uint4 v;

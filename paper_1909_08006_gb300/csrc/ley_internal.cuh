@@ -39,6 +39,7 @@ constexpr int kFinItems = 8;
 constexpr int kSmall = kFinThreads * kFinItems;        // 2048 tuples: big-bucket threshold
 constexpr int kTiny = 32;                              // tiny-bucket threshold (comparison rank)
 constexpr int kWarpMax = 32 * kFinItems;               // sub-buckets one warp sorts (256)
+constexpr uint32_t kFlagPiece = 8 * kSmall;              // pieces of an all-equal run (16384)
 // Sub-buckets above kTiny inside one task are disjoint at each digit depth,
 // so at most kSmall / (kTiny + 1) per depth and kMaxDigits depths: the
 // queue never needs more slots than this and never wraps.

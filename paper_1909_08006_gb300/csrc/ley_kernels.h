@@ -30,6 +30,10 @@ cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int l
 cudaError_t launch_classify_partition(cudaStream_t s, const Work& w);
 cudaError_t launch_pass(const LaunchCfg& c, const Work& w, KeySpec ks, int level);
 cudaError_t launch_finish_records(const LaunchCfg& c, const Work& w, KeySpec ks);
+// Finish + record gather in one kernel (100-byte records): out[j] is written
+// directly, no permutation; source indices are < n_in.
+cudaError_t launch_finish_gather(const LaunchCfg& c, const Work& w, KeySpec ks, const uint8_t* in,
+                                 uint8_t* out, unsigned long long n_in);
 cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, uint64_t* keys_out,
                                 uint32_t* idx_out);
 // out[j] = in[perm[j]] for j < n; perm entries are < n_in (records at `in`).
@@ -53,7 +57,7 @@ cudaError_t launch_tuple_index(cudaStream_t s, int grid, const uint4* t, uint32_
 // Occupancy-derived persistent grid sizes (blocks per SM) for a kernel kind.
 enum KernelKind {
     KK_EXTRACT_REC = 0, KK_EXTRACT_PAIRS, KK_HIST, KK_SCAN, KK_PASS, KK_FINISH_REC, KK_FINISH_PAIRS,
-    KK_GATHER100, KK_GATHER100_TMA, KK_GATHER_GENERIC, KK_COUNT
+    KK_GATHER100, KK_GATHER100_TMA, KK_GATHER_GENERIC, KK_FINISH_GATHER, KK_COUNT
 };
 int blocks_per_sm(KernelKind k);
 size_t kernel_smem(KernelKind k);

@@ -17,9 +17,13 @@
 //   k_finish      the small-bucket queue: one CTA per task sorts it in shared
 //                 memory by MSD counting passes, with comparison ranking for
 //                 tiny sub-buckets (SingleThreadRadixSort / ComparisonSort of
-//                 Algorithm 1), and emits the final permutation.
+//                 Algorithm 1), and emits the final permutation -- or, for
+//                 100-byte records, gathers the records themselves into
+//                 place (the record scatter of Section 3.2, fused).
 #define LEY_FILE_ID 1
 #include "ley_kernels.h"
+#include "ley_rec100.cuh"
+#include "ley_tma.cuh"
 
 namespace ley {
 
@@ -448,19 +452,25 @@ k_scan(Work w, int L) {
 
 // ------------------------------------------------------------- classify
 
+// A finishing task.  A run whose keys are all equal (flags 1) is already in
+// order and may be of any size; it is cut into pieces of at most kFlagPiece
+// so that its output is written by many CTAs at once.
 __device__ void emit_fin(const Work& w, ull start, uint32_t count, int digit, int buf, int flags) {
-    ull slot = atomicAdd(&w.ctl->fin_count, 1ull);
-    if (slot >= w.cap_fin) {
-        LEY_FAIL(w.err, kErrCapacity);
-        return;
+    const uint32_t pieces = (flags & 1) ? (count + kFlagPiece - 1) / kFlagPiece : 1u;
+    const ull slot = atomicAdd(&w.ctl->fin_count, (ull)pieces);
+    for (uint32_t i = 0; i < pieces; i++) {
+        if (slot + i >= w.cap_fin) {
+            LEY_FAIL(w.err, kErrCapacity);
+            return;
+        }
+        FinTask f;
+        f.start = start + (ull)i * kFlagPiece;
+        f.count = (flags & 1) ? min(count - i * kFlagPiece, (uint32_t)kFlagPiece) : count;
+        f.digit = (uint16_t)digit;
+        f.buf = (uint8_t)buf;
+        f.flags = (uint8_t)flags;
+        w.fin[slot + i] = f;
     }
-    FinTask f;
-    f.start = start;
-    f.count = count;
-    f.digit = (uint16_t)digit;
-    f.buf = (uint8_t)buf;
-    f.flags = (uint8_t)flags;
-    w.fin[slot] = f;
 }
 
 // Appends a bucket to the next level's big list (called by a whole warp with
@@ -854,6 +864,13 @@ struct Emitter<1> {  // pairs: sorted keys and their payloads
     }
 };
 
+template <>
+struct Emitter<2> {  // 100-byte records gathered straight into place
+    const uint8_t* in;
+    uint8_t* out;
+    ull n_in;        // records at `in`: every source index is below it
+};
+
 // Shared state of one finishing CTA.  B holds the task's tuples; order[j] is
 // the position in B of the tuple whose final place in the task is j.
 struct FinShared {
@@ -1185,6 +1202,92 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
     }
 }
 
+// Record gather of one finished task: out[start + j] = in[src index of j]
+// for j < count, where the source index is sidx[j] (shared memory), or
+// src[j].w when the task's tuples are already in order (flagged).  Rounds of
+// kFinThreads records, one per thread: the record's 112-byte window is
+// bulk-copied (TMA) into B; then each warp shifts its 32 records in place
+// into 3200 contiguous output bytes and writes them as one bulk store of the
+// 16-byte aligned middle plus word stores of the ragged ends.  The staged
+// output starts at its own 16-byte phase (ph) inside the warp's window area,
+// so the aligned middle is aligned in shared memory too.  Returns false (all
+// threads alike) if a bulk copy did not land within the wait limit.
+__device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint4* src,
+                                   bool flagged, ull start, uint32_t count, const Emitter<2>& e,
+                                   uint64_t* bar, uint32_t& phase, uint32_t* err) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* wreg = Bb + warp * (32 * kWinBytes);  // this warp's 32 windows
+    const uint32_t* wsrc = reinterpret_cast<const uint32_t*>(wreg);
+    for (uint32_t r0 = 0; r0 < count; r0 += kFinThreads) {
+        const uint32_t nv = min(count - r0, (uint32_t)kFinThreads);
+        const uint32_t j = r0 + tid;
+        // B's previous contents (tuples, or the last round's output, whose
+        // bulk stores have been read out) are no longer used.
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) mbar_arrive_expect_tx(bar, nv * kWinBytes);
+        uint32_t o = 0;
+        if (j < count) {
+            uint32_t p = flagged ? src[j].w : sidx[j];
+            if (p >= e.n_in) {  // never for a valid task list; keeps reads in bounds
+                LEY_FAIL(err, kErrCapacity);
+                p = 0;
+            }
+            const ull sb = (ull)p * kRec;
+            o = (uint32_t)(sb & 15) >> 2;
+            tma_load_1d(Bb + tid * kWinBytes, e.in + (sb & ~15ull), kWinBytes, bar);
+        }
+        const bool landed = mbar_wait(bar, phase);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) LEY_FAIL(err, kErrTimeout);
+            (void)mbar_wait(bar, phase);  // a bounded chance for copies in flight
+            return false;
+        }
+        phase ^= 1u;
+        const uint32_t wr0 = (uint32_t)warp * 32;
+        if (wr0 < nv) {  // warp-uniform
+            const uint32_t words = min(nv - wr0, 32u) * kRecWords;
+            const ull g0 = (start + r0 + wr0) * kRec, g1 = g0 + 4ull * words;
+            const uint32_t ph = (uint32_t)(g0 & 15);  // 0, 4, 8 or 12
+            uint32_t* wdst = reinterpret_cast<uint32_t*>(wreg + ph);
+            // Output word q (record k = q / 25, word i) comes from window word
+            // 28k + o_k + i.  Past record 0 the source never lies below the
+            // destination, and record 0 is copied within the first step, so
+            // a forward copy in steps of 32 words (all reads of a step before
+            // its writes) is safe in place.
+            for (uint32_t q0 = 0; q0 < words; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const uint32_t k = q / kRecWords;
+                const uint32_t ok = __shfl_sync(0xffffffffu, o, k & 31);
+                uint32_t val = 0;
+                if (q < words) val = wsrc[k * (kWinBytes / 4) + ok + (q - k * kRecWords)];
+                __syncwarp();
+                if (q < words) wdst[q] = val;
+                __syncwarp();
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            const ull a0 = (g0 + 15) & ~15ull, a1 = g1 & ~15ull;
+            uint32_t* outw = reinterpret_cast<uint32_t*>(e.out + g0);
+            if (a1 > a0) {
+                const uint32_t head = (uint32_t)(a0 - g0) >> 2;
+                const uint32_t tail0 = (uint32_t)(a1 - g0) >> 2, tail = words - tail0;
+                if ((uint32_t)lane < head) outw[lane] = wdst[lane];
+                if (lane >= 8 && (uint32_t)lane - 8 < tail) outw[tail0 + lane - 8] = wdst[tail0 + lane - 8];
+                if (lane == 0) {
+                    tma_store_1d(e.out + a0, reinterpret_cast<uint8_t*>(wdst) + (a0 - g0),
+                                 (uint32_t)(a1 - a0));
+                    bulk_commit();
+                }
+            } else {
+                for (uint32_t q = lane; q < words; q += 32) outw[q] = wdst[q];
+            }
+        }
+        if (lane == 0) bulk_wait_read_0();  // B is reused by the next round or task
+    }
+    return true;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kFinThreads, 4)
 k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
@@ -1192,8 +1295,16 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     __shared__ FinShared S;
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
+    __shared__ __align__(8) uint64_t gbar;  // MODE 2: the record windows' bulk copies
+    uint32_t gphase = 0;
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
-    if (tid == 0) S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
+    if (tid == 0) {
+        S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
+        if (MODE == 2) {
+            mbar_init(&gbar, 1);
+            mbar_fence_init();
+        }
+    }
     LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
@@ -1217,7 +1328,13 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
         }
         const uint4* src = w.tup[tk.buf & 1] + tk.start;
         if (!skip && (tk.flags & 1)) {  // all keys equal: input order
-            for (uint32_t i = tid; i < tk.count; i += kFinThreads) emit(tk.start + i, src[i]);
+            if constexpr (MODE == 2) {
+                if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), nullptr, src, true,
+                                        tk.start, tk.count, emit, &gbar, gphase, w.err))
+                    break;
+            } else {
+                for (uint32_t i = tid; i < tk.count; i += kFinThreads) emit(tk.start + i, src[i]);
+            }
             skip = true;
         }
         if (!skip) {
@@ -1246,14 +1363,32 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                 __syncthreads();
             }
             LEY_PHASE(13);
-            // Coalesced write of the task's final order.
-            for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
-                uint32_t o = S.order[j];
-                if (o >= tk.count) {  // a position left unset: report, stay in bounds
-                    LEY_FAIL(w.err, kErrCapacity);
-                    o = 0;
+            if constexpr (MODE == 2) {
+                // The task's source indices in final order (count <= kSmall
+                // entries over the counters, which are free now), then the
+                // records themselves.
+                uint32_t* sidx = &S.cnt[0][0];
+                for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
+                    uint32_t o = S.order[j];
+                    if (o >= tk.count) {  // a position left unset: report, stay in bounds
+                        LEY_FAIL(w.err, kErrCapacity);
+                        o = 0;
+                    }
+                    sidx[j] = B[o].w;
                 }
-                emit(tk.start + j, B[o]);
+                if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), sidx, src, false,
+                                        tk.start, tk.count, emit, &gbar, gphase, w.err))
+                    break;
+            } else {
+                // Coalesced write of the task's final order.
+                for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
+                    uint32_t o = S.order[j];
+                    if (o >= tk.count) {  // a position left unset: report, stay in bounds
+                        LEY_FAIL(w.err, kErrCapacity);
+                        o = 0;
+                    }
+                    emit(tk.start + j, B[o]);
+                }
             }
             LEY_PHASE(14);
         }
@@ -1346,6 +1481,16 @@ cudaError_t launch_finish_records(const LaunchCfg& c, const Work& w, KeySpec ks)
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish_gather(const LaunchCfg& c, const Work& w, KeySpec ks, const uint8_t* in,
+                                 uint8_t* out, ull n_in) {
+    Emitter<2> e;
+    e.in = in;
+    e.out = out;
+    e.n_in = n_in;
+    k_finish<2><<<c.grid, kFinThreads, c.smem, c.stream>>>(w, ks, e);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, uint64_t* keys_out,
                                 uint32_t* idx_out) {
     Emitter<1> e;
@@ -1369,7 +1514,8 @@ size_t kernel_smem(KernelKind k) {
     switch (k) {
         case KK_PASS: return (size_t)kPassTile * sizeof(uint4);
         case KK_FINISH_REC:
-        case KK_FINISH_PAIRS: return (size_t)kSmall * sizeof(uint4);
+        case KK_FINISH_PAIRS:
+        case KK_FINISH_GATHER: return (size_t)kSmall * sizeof(uint4);
         default: return 0;
     }
 }
@@ -1379,7 +1525,8 @@ int kernel_threads(KernelKind k) {
         case KK_PASS: return kPassThreads;
         case KK_HIST: return kHistThreads;
         case KK_FINISH_REC:
-        case KK_FINISH_PAIRS: return kFinThreads;
+        case KK_FINISH_PAIRS:
+        case KK_FINISH_GATHER: return kFinThreads;
         default: return 256;
     }
 }
@@ -1395,6 +1542,8 @@ int blocks_per_sm(KernelKind k) {
                              (int)kernel_smem(KK_FINISH_REC));
         cudaFuncSetAttribute(k_finish<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kernel_smem(KK_FINISH_PAIRS));
+        cudaFuncSetAttribute(k_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kernel_smem(KK_FINISH_GATHER));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_extract_records<100>, 256, 0);
         g_bps[KK_EXTRACT_REC] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_extract_pairs, 256, 0);
@@ -1412,6 +1561,9 @@ int blocks_per_sm(KernelKind k) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_finish<1>, kFinThreads,
                                                       kernel_smem(KK_FINISH_PAIRS));
         g_bps[KK_FINISH_PAIRS] = v > 0 ? v : 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_finish<2>, kFinThreads,
+                                                      kernel_smem(KK_FINISH_GATHER));
+        g_bps[KK_FINISH_GATHER] = v > 0 ? v : 1;
         g_bps[KK_GATHER100] = gather_blocks_per_sm(KK_GATHER100);
         g_bps[KK_GATHER100_TMA] = gather_blocks_per_sm(KK_GATHER100_TMA);
         g_bps[KK_GATHER_GENERIC] = gather_blocks_per_sm(KK_GATHER_GENERIC);

@@ -45,8 +45,12 @@ def test_host_only_entry_points(ley):
     assert ley.ley_status_string(99) == "unknown status"
     assert ley.ley_workspace_bytes(0) == 0
     b = ley.ley_workspace_bytes(100_000_000)
-    # two 16-byte tuple buffers + a 4-byte permutation per record, plus control
-    assert 36 * 100_000_000 < b < 42 * 100_000_000
+    # 100-byte records are gathered inside the finishing kernel: two 16-byte
+    # tuple buffers per record, plus control
+    assert 32 * 100_000_000 < b < 38 * 100_000_000
+    # other record sizes also hold a 4-byte permutation per record
+    b104 = ley.ley_workspace_bytes(100_000_000, rec_bytes=104)
+    assert b104 - b == 4 * 100_000_000
     with pytest.raises(ley.LeyError) as e:
         ley.ley_workspace_bytes(10, rec_bytes=100, key_bytes=13)
     assert e.value.status == ley.LEY_EUNSUPPORTED

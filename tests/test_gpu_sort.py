@@ -119,6 +119,38 @@ def test_lsu_gather_variant_exact(orc, ley, monkeypatch):
         check_exact(orc, ley, datagen.uniform_records(n, seed=n + 5))
 
 
+def test_separate_tma_gather_variant_exact(orc, ley, monkeypatch):
+    # the finish kernel writes a permutation and a separate TMA kernel gathers
+    monkeypatch.setenv("LEY_GATHER", "tma")
+    for n in [1, 31, 33, 4096, 100_003]:
+        check_exact(orc, ley, datagen.uniform_records(n, seed=n + 6))
+    check_exact(orc, ley, datagen.edge_records("equal", 40_000, seed=4))
+
+
+@pytest.mark.parametrize("kind", ["equal", "few_distinct"])
+def test_long_equal_runs_exact(orc, ley, kind):
+    # runs of equal keys far longer than one finishing task, cut into pieces
+    # with a ragged last piece
+    check_exact(orc, ley, datagen.edge_records(kind, 1_000_003, seed=8))
+
+
+@pytest.mark.parametrize("in_off,out_off", [(16, 48), (48, 16), (112, 0)])
+def test_buffers_at_16_byte_offsets(orc, ley, in_off, out_off):
+    # record arrays that start 16-byte aligned but not 128- or 256-byte aligned
+    n = 70_001
+    rec = datagen.uniform_records(n, seed=in_off + out_off)
+    big_in = torch.zeros(n * 100 + 256, dtype=torch.uint8, device=DEV)
+    big_out = torch.zeros(n * 100 + 256, dtype=torch.uint8, device=DEV)
+    d_in = big_in[in_off:in_off + n * 100].view(n, 100)
+    d_in.copy_(rec.to(DEV))
+    d_out = big_out[out_off:out_off + n * 100].view(n, 100)
+    ley.ley_sort_records(d_in, d_out)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(rec.numpy(), key_bytes=10))
+    # nothing outside the output records was written
+    assert not big_out[:out_off].any() and not big_out[out_off + n * 100:].any()
+
+
 def test_repeated_calls_same_answer(orc, ley):
     rec = datagen.skew_records(50_000, seed=11)
     a = gpu_sort(ley, rec)
