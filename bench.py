@@ -341,6 +341,41 @@ def run_pairs(args, world, rank, dev, stream, pg):
     }
 
 
+def _libcuda():
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    cu.cuMemHostAlloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_uint]
+    cu.cuMemFreeHost.argtypes = [ctypes.c_void_p]
+    return cu
+
+
+_HOST_BUFS = {}
+
+
+def host_alloc(nbytes):
+    """Exact-size page-locked host buffer from cuMemHostAlloc, as a numpy
+    array (torch's pinned pool rounds up to 2^k bytes).  Memory registered with
+    cudaHostRegister instead was measured to copy at only ~122 GB/s each way
+    in full duplex on GB300, against ~172 GB/s for cuMemHostAlloc memory."""
+    import ctypes
+    import numpy as np
+    import torch
+    torch.cuda.init()
+    cu = _libcuda()
+    p = ctypes.c_void_p()
+    rc = cu.cuMemHostAlloc(ctypes.byref(p), nbytes, 0)
+    if rc != 0:
+        raise RuntimeError(f"cuMemHostAlloc({nbytes}) failed ({rc})")
+    a = np.ctypeslib.as_array((ctypes.c_uint8 * nbytes).from_address(p.value))
+    _HOST_BUFS[a.ctypes.data] = p
+    return a
+
+
+def host_free(a):
+    p = _HOST_BUFS.pop(a.ctypes.data)
+    _libcuda().cuMemFreeHost(p)
+
+
 def run_host_mode(args, world, rank, dev, stream, pg):
     """Records in pinned host memory, sorted to pinned host memory under a
     device budget: the partially in-memory sort (input resident on the device)
@@ -350,17 +385,7 @@ def run_host_mode(args, world, rank, dev, stream, pg):
     import paper_1909_08006_gb300 as ley
     import numpy as np
     n, budget = args.n, int(args.budget_gb * 1e9)
-    cudart = torch.cuda.cudart()
-
-    def pinned(nbytes):
-        # exact-size page-locked buffer (torch's pinned pool rounds up to 2^k)
-        a = np.empty(nbytes, dtype=np.uint8)
-        rc = cudart.cudaHostRegister(a.ctypes.data, nbytes, 0)
-        if int(rc) != 0:
-            raise RuntimeError(f"cudaHostRegister failed ({rc})")
-        return a
-
-    h_in_np, h_out_np = pinned(n * REC), pinned(n * REC)
+    h_in_np, h_out_np = host_alloc(n * REC), host_alloc(n * REC)
     h_in = torch.from_numpy(h_in_np).view(n, REC)
     h_out = torch.from_numpy(h_out_np).view(n, REC)
     chunk = 50_000_000
@@ -379,8 +404,9 @@ def run_host_mode(args, world, rank, dev, stream, pg):
     dt = max_over_ranks((time.perf_counter() - t0) / steps, pg, dev)
     ws = ley.ley_workspace_bytes(n)
     mode = "partial" if n * REC + ws <= budget else "external"
-    for a in (h_in_np, h_out_np):
-        cudart.cudaHostUnregister(a.ctypes.data)
+    del h_in, h_out
+    host_free(h_in_np)
+    host_free(h_out_np)
     link = 2 * n * REC if mode == "partial" else 4 * n * REC
     return {
         "metric": f"GB/s of 100-byte records sorted host-to-host ({mode}, device budget)",

@@ -20,9 +20,11 @@
  *  - Device buffers must be 16-byte aligned.  Inputs are never written.
  *    Output buffers must not overlap inputs.
  *  - The caller owns all buffers it passes.  The library allocates its own
- *    scratch stream-ordered (cudaMallocAsync on `stream`) and frees it before
- *    the call's work ends; every scratch byte counts against `mem_budget`
- *    (0 = no cap).
+ *    scratch stream-ordered on `stream` from a per-device memory pool of its
+ *    own and frees it before the call's work ends; every scratch byte counts
+ *    against `mem_budget` (0 = no cap).  The pool keeps freed memory mapped
+ *    for later calls, and external sorts keep their pinned host scratch (the
+ *    sorted runs), until ley_release_cache().
  *  - Errors found on the host are returned before any work is queued.  Errors
  *    found by a kernel (a bounded wait that gave up) are latched in a
  *    per-device status word read by ley_last_device_status().
@@ -123,6 +125,14 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
  */
 ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
                                uint64_t* bytes);
+
+/*
+ * Returns the memory this library keeps between calls: the unused part of
+ * each device's scratch pool and the pinned host scratch of the external
+ * sort.  Call it when no sort of this library is running (on any stream);
+ * later sorts allocate again.
+ */
+ley_status ley_release_cache(void);
 
 /* Static English text for a status code (never NULL). */
 const char* ley_status_string(ley_status s);

@@ -77,6 +77,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_merge_records.restype = ctypes.c_int
     lib.ley_sort_records_noalloc.argtypes = [vp, vp, u64, u32, u32, vp]
     lib.ley_sort_records_noalloc.restype = ctypes.c_int
+    lib.ley_release_cache.argtypes = []
+    lib.ley_release_cache.restype = ctypes.c_int
     return lib
 
 
@@ -203,6 +205,11 @@ def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10) -> in
     _check(_lib.ley_workspace_bytes(n, rec_bytes, key_bytes, ctypes.byref(v)),
            "ley_workspace_bytes")
     return int(v.value)
+
+
+def ley_release_cache() -> int:
+    """Return the device pool memory and pinned host scratch kept between calls."""
+    return _check(_lib.ley_release_cache(), "ley_release_cache")
 
 
 def ley_status_string(status: int) -> str:

@@ -2,11 +2,13 @@
 // the internal sort, and the host-memory (partially in-memory) mode.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "leysort.h"
@@ -22,6 +24,10 @@ struct DevState {
     bool init = false;
     int sms = 0;
     uint32_t* err = nullptr;
+    // The library's scratch comes from its own stream-ordered pool, which
+    // keeps freed memory mapped for the next call (re-mapping tens of GB on
+    // every call costs tens of milliseconds); ley_release_cache() trims it.
+    cudaMemPool_t pool = nullptr;
 };
 static DevState g_dev[64];
 static std::mutex g_mu;
@@ -58,11 +64,30 @@ static DevState* dev_state() {
         if (cudaMalloc(&p, 256) != cudaSuccess) return nullptr;
         if (cudaMemset(p, 0, 256) != cudaSuccess) return nullptr;
         s.err = static_cast<uint32_t*>(p);
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = d;
+        if (cudaMemPoolCreate(&s.pool, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolSetAttribute(s.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+            return nullptr;
         (void)blocks_per_sm(KK_PASS);  // occupancy tables and smem attributes
         set_l2_fetch_granularity();
         s.init = true;
     }
     return &s;
+}
+
+// Stream-ordered scratch from the device's library pool.
+static bool scratch_alloc(DevState* ds, void** p, size_t bytes, cudaStream_t st) {
+    if (cudaMallocFromPoolAsync(p, bytes, ds->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
 }
 
 uint32_t* device_err_word() {
@@ -363,10 +388,7 @@ static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st
     const Layout L = make_layout(a.n, a.mode == MODE_RECORDS && !fused_gather(a.rec));
     if (budget && L.total > budget) return LEY_ENOMEM;
     void* base = nullptr;
-    if (cudaMallocAsync(&base, L.total, st) != cudaSuccess) {
-        cudaGetLastError();
-        return LEY_ENOMEM;
-    }
+    if (!scratch_alloc(ds, &base, L.total, st)) return LEY_ENOMEM;
     ley_status s = enqueue_sort(a, static_cast<char*>(base), L, st, ds);
     cudaFreeAsync(base, st);
     return s;
@@ -378,17 +400,30 @@ static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st
 // threads of Section 3.2 become two copy streams beside the compute stream).
 struct HostPipe {
     cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t gth = nullptr;  // record gathers into the copy-out staging buffers
     std::vector<cudaEvent_t> evs;
     bool ok = true;
     explicit HostPipe(cudaStream_t st) {
         ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+             cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&gth, cudaStreamNonBlocking) == cudaSuccess;
         if (ok) {
             cudaEvent_t e = ev();  // side streams start after the caller's prior work
             ok = e && cudaEventRecord(e, st) == cudaSuccess &&
                  cudaStreamWaitEvent(h2d, e, 0) == cudaSuccess &&
-                 cudaStreamWaitEvent(d2h, e, 0) == cudaSuccess;
+                 cudaStreamWaitEvent(d2h, e, 0) == cudaSuccess &&
+                 cudaStreamWaitEvent(gth, e, 0) == cudaSuccess;
         }
+    }
+    // `s` waits for event e (if any).
+    bool wait(cudaStream_t s, cudaEvent_t e) {
+        return !e || cudaStreamWaitEvent(s, e, 0) == cudaSuccess;
+    }
+    // An event recorded on s now.
+    cudaEvent_t record(cudaStream_t s) {
+        cudaEvent_t e = ev();
+        if (e && cudaEventRecord(e, s) != cudaSuccess) return nullptr;
+        return e;
     }
     cudaEvent_t ev() {
         cudaEvent_t e = nullptr;
@@ -402,12 +437,42 @@ struct HostPipe {
         return e && cudaEventRecord(e, from) == cudaSuccess &&
                cudaStreamWaitEvent(to, e, 0) == cudaSuccess;
     }
+    // LEY_TRACE=1: timestamps of marked points on each stream, printed to
+    // stderr (milliseconds from the first mark) when the sort ends.
+    struct Mark {
+        std::string what;
+        cudaEvent_t e;
+    };
+    std::vector<Mark> marks;
+    const bool trace = std::getenv("LEY_TRACE") != nullptr;
+    void mark(cudaStream_t s, const char* what, long i = -1) {
+        if (!trace) return;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, s);
+        std::string w = what;
+        if (i >= 0) w += " " + std::to_string(i);
+        w += s == h2d ? " [h2d]" : (s == d2h ? " [d2h]" : (s == gth ? " [gather]" : " [compute]"));
+        marks.push_back({w, e});
+    }
     ~HostPipe() {
         if (h2d) cudaStreamSynchronize(h2d);
         if (d2h) cudaStreamSynchronize(d2h);
+        if (gth) cudaStreamSynchronize(gth);
+        if (!marks.empty()) {
+            cudaEventSynchronize(marks.back().e);
+            for (auto& m : marks) {
+                float ms = 0.f;
+                cudaEventSynchronize(m.e);
+                cudaEventElapsedTime(&ms, marks[0].e, m.e);
+                std::fprintf(stderr, "leysort trace %9.3f ms  %s\n", ms, m.what.c_str());
+            }
+            for (auto& m : marks) cudaEventDestroy(m.e);  // after the last use of marks[0]
+        }
         for (auto e : evs) cudaEventDestroy(e);
         if (h2d) cudaStreamDestroy(h2d);
         if (d2h) cudaStreamDestroy(d2h);
+        if (gth) cudaStreamDestroy(gth);
     }
 };
 
@@ -438,7 +503,7 @@ static ley_status stream_out(const SortArgs& a, const uint32_t* perm, ull j0, ul
 static ley_status stream_in_extract(const SortArgs& a, const uint8_t* host_in, uint8_t* dev,
                                     const Work& w, const KeySpec& ks, cudaStream_t st,
                                     HostPipe& hp, int sms) {
-    const ull chunk = (ull)kPassTile * 256;  // ~100 MB of 100-byte records
+    const ull chunk = (ull)kPassTile * 1024;  // ~400 MB of 100-byte records
     for (ull c0 = 0; c0 < a.n; c0 += chunk) {
         const ull c1 = c0 + chunk < a.n ? c0 + chunk : a.n;
         LEY_TRY(cudaMemcpyAsync(dev + c0 * a.rec, host_in + c0 * a.rec, (c1 - c0) * a.rec,
@@ -476,10 +541,7 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
     const size_t need = align_up(bytes, 256) + L.total + 2 * stg_bytes;
     if (budget && need > budget) return LEY_ENOMEM;
     void* dmem = nullptr;
-    if (cudaMallocAsync(&dmem, need, st) != cudaSuccess) {
-        cudaGetLastError();
-        return LEY_ENOMEM;
-    }
+    if (!scratch_alloc(ds, &dmem, need, st)) return LEY_ENOMEM;
     char* din = static_cast<char*>(dmem);
     char* ws = din + align_up(bytes, 256);
     uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
@@ -492,11 +554,17 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         d.in = reinterpret_cast<const uint8_t*>(din);
         Work w = make_work(ws, L, a.n, ds->err);
         const KeySpec ks = record_keyspec(a.kb);
+        hp.mark(hp.h2d, "in begin");
         if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
         if (s == LEY_OK) s = stream_in_extract(d, a.in, reinterpret_cast<uint8_t*>(din), w, ks, st, hp, ds->sms);
+        hp.mark(hp.h2d, "in end");
+        hp.mark(st, "extracted");
         if (s == LEY_OK) s = stage_levels_finish(d, w, ks, st, ds->sms);
+        hp.mark(st, "sorted");
         cudaEvent_t stg_free[2] = {nullptr, nullptr};
         if (s == LEY_OK) s = stream_out(d, w.perm, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
+        hp.mark(st, "gathered");
+        hp.mark(hp.d2h, "out end");
         if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
         cudaFreeAsync(dmem, st);
         if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
@@ -568,11 +636,28 @@ static std::vector<std::vector<ull>> plan_partitions(const std::vector<HostRun>&
         if (x.run != y.run) return x.run < y.run;
         return x.pos < y.pos;
     });
-    for (auto& c : cands) {
-        ull r = 0;
-        for (size_t i = 0; i < k; i++)
-            r += corank_split(runs, i, runs[c.run].base + c.pos * rec, c.run, c.pos, rec, kb);
-        c.rank = r;
+    // Each candidate's rank costs k binary searches over host memory, bound
+    // by memory latency: spread the candidates over the host's cores.
+    auto rank_range = [&](size_t c0, size_t c1) {
+        for (size_t ci = c0; ci < c1; ci++) {
+            Cand& c = cands[ci];
+            ull r = 0;
+            for (size_t i = 0; i < k; i++)
+                r += corank_split(runs, i, runs[c.run].base + c.pos * rec, c.run, c.pos, rec, kb);
+            c.rank = r;
+        }
+    };
+    const size_t nthr = std::max<size_t>(1, std::min<size_t>(16, std::thread::hardware_concurrency()));
+    if (nthr == 1 || cands.size() < 64) {
+        rank_range(0, cands.size());
+    } else {
+        std::vector<std::thread> pool;
+        const size_t per = (cands.size() + nthr - 1) / nthr;
+        for (size_t t = 0; t < nthr; t++) {
+            const size_t c0 = t * per, c1 = std::min(cands.size(), c0 + per);
+            if (c0 < c1) pool.emplace_back(rank_range, c0, c1);
+        }
+        for (auto& th : pool) th.join();
     }
     std::vector<std::vector<ull>> cuts;
     cuts.push_back(std::vector<ull>(k, 0));
@@ -614,7 +699,9 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
     if (s != LEY_OK) return s;
     s = stage_extract_records(m, w, ks, st, sms, 0, 0, ceil_div_u64(m.n, kPassTile));
     if (s != LEY_OK) return s;
-    LEY_TRY(cudaMemcpyAsync(off_dev, off_host, sizeof(ull) * (k + 1), cudaMemcpyHostToDevice, st));
+    LEY_TRY(launch("merge_offsets", st, [&] {
+        return launch_set_offsets(st, off_dev, off_host, k + 1);
+    }));
     int cur = 0;
     for (uint32_t runs = k; runs > 1; runs = (runs + 1) / 2) {
         LEY_TRY(launch("merge", st, [&] {
@@ -635,12 +722,20 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
     return LEY_OK;
 }
 
-// External sort (Section 3.2, Figure 1): runs of r_len records are copied in
-// on the reader stream, sorted by the internal sort and streamed into pinned
-// host scratch on the writer stream, overlapped run by run; the merge stage
-// then cuts the output into partitions by k-way co-rank, copies each
-// partition's slices of every run in, merges them by merge path, gathers the
-// records and streams them to `out`, again overlapped partition by partition.
+// External sort (Section 3.2, Figure 1).  Run formation: runs of r_len
+// records are copied in on the reader stream (extraction following chunk by
+// chunk), sorted on the compute stream, and gathered into staging buffers on
+// the gather stream that the writer stream copies into pinned host scratch.
+// Merge: the output is cut into partitions by k-way co-rank; each partition's
+// slices of every run are copied in, merged by merge path, gathered and
+// streamed to `out`.  Two record buffers and two workspaces alternate, so one
+// run (or partition) streams out while the next is copied in and sorted, and
+// runs are about n / kExtRuns records, so that filling and draining this
+// pipeline (the first copy in, the last copy out) costs little next to the
+// copies themselves.
+constexpr ull kExtRuns = 16;
+constexpr ull kExtMinRun = 4ull << 20;
+
 static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t st) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
@@ -648,21 +743,26 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     const size_t stg_bytes = align_up(q * a.rec, 256);
     const size_t fixed = 2 * stg_bytes + 64 * 1024;
     if (budget <= fixed) return LEY_ENOMEM;
-    // largest run (whole tiles) whose two input buffers and workspace fit
-    auto need = [&](ull r) { return 2 * align_up(r * a.rec, 256) + make_layout(r, true).total + fixed; };
+    // largest run (whole tiles) whose two record buffers and two workspaces fit
+    auto need = [&](ull r) {
+        return 2 * align_up(r * a.rec, 256) + 2 * make_layout(r, true).total + fixed;
+    };
     ull lo = 0, hi = a.n / kPassTile + 1;
     while (lo < hi) {
         const ull mid = (lo + hi + 1) / 2;
         if (need(mid * kPassTile) <= budget) lo = mid;
         else hi = mid - 1;
     }
-    const ull r_len = lo * kPassTile;
-    if (r_len == 0) return LEY_ENOMEM;
+    const ull r_max = lo * kPassTile;
+    if (r_max == 0) return LEY_ENOMEM;
+    ull r_len = ceil_div_u64(ceil_div_u64(a.n, kExtRuns), kPassTile) * kPassTile;
+    if (r_len < kExtMinRun) r_len = kExtMinRun;
+    if (r_len > r_max) r_len = r_max;
     const uint32_t k = (uint32_t)((a.n + r_len - 1) / r_len);
     if (k > 128) return LEY_ENOMEM;  // budget too small for the merge fan-in
     const Layout L = make_layout(r_len, true);
     const size_t in_bytes = align_up(r_len * a.rec, 256);
-    const size_t total = 2 * in_bytes + L.total + 2 * stg_bytes + 8 * 1024;
+    const size_t total = 2 * in_bytes + 2 * L.total + 2 * stg_bytes + 8 * 1024;
     const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
     if (dbg)
         std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
@@ -672,22 +772,21 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     uint8_t* hs = host_scratch(a.n * a.rec);
     if (!hs) return LEY_ENOMEM;
     void* dmem = nullptr;
-    if (cudaMallocAsync(&dmem, total, st) != cudaSuccess) {
-        cudaGetLastError();
-        return LEY_ENOMEM;
-    }
+    if (!scratch_alloc(ds, &dmem, total, st)) return LEY_ENOMEM;
     char* base = static_cast<char*>(dmem);
     uint8_t* dbuf[2] = {reinterpret_cast<uint8_t*>(base), reinterpret_cast<uint8_t*>(base + in_bytes)};
-    char* ws = base + 2 * in_bytes;
-    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
-                       reinterpret_cast<uint8_t*>(ws + L.total + stg_bytes)};
-    ull* off_dev = reinterpret_cast<ull*>(ws + L.total + 2 * stg_bytes);
+    char* ws[2] = {base + 2 * in_bytes, base + 2 * in_bytes + L.total};
+    char* tail = base + 2 * in_bytes + 2 * L.total;
+    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(tail), reinterpret_cast<uint8_t*>(tail + stg_bytes)};
+    ull* off_dev = reinterpret_cast<ull*>(tail + 2 * stg_bytes);
     ley_status s = LEY_OK;
     {
         HostPipe hp(st);
         if (!hp.ok) s = LEY_ECUDA;
         const KeySpec ks = record_keyspec(a.kb);
         cudaEvent_t stg_free[2] = {nullptr, nullptr};
+        // buffer b and workspace b are free again once the gathers that read
+        // them (two runs or partitions back) are done
         cudaEvent_t buf_free[2] = {nullptr, nullptr};
         // --- run formation
         std::vector<HostRun> runs;
@@ -695,32 +794,39 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
             const ull r0 = (ull)r * r_len;
             const ull rn = a.n - r0 < r_len ? a.n - r0 : r_len;
             const int b = r & 1;
-            if (buf_free[b] && cudaStreamWaitEvent(hp.h2d, buf_free[b], 0) != cudaSuccess) s = LEY_ECUDA;
+            if (!hp.wait(hp.h2d, buf_free[b]) || !hp.wait(st, buf_free[b])) s = LEY_ECUDA;
             SortArgs ra = a;
             ra.in = dbuf[b];
             ra.n = rn;
-            Work w = make_work(ws, L, rn, ds->err);
+            Work w = make_work(ws[b], L, rn, ds->err);
+            hp.mark(hp.h2d, "run in begin", r);
             if (s == LEY_OK) s = stage_prepare(w, L, st, rn, 0);
             if (s == LEY_OK) s = stream_in_extract(ra, a.in + r0 * a.rec, dbuf[b], w, ks, st, hp, ds->sms);
+            hp.mark(hp.h2d, "run in end", r);
             if (s == LEY_OK) s = stage_levels_finish(ra, w, ks, st, ds->sms);
-            if (s == LEY_OK) s = stream_out(ra, w.perm, 0, rn, hs + r0 * a.rec, stg, q, st, hp, stg_free, ds->sms);
-            if (s == LEY_OK) {
-                buf_free[b] = hp.ev();
-                if (!buf_free[b] || cudaEventRecord(buf_free[b], st) != cudaSuccess) s = LEY_ECUDA;
-            }
+            hp.mark(st, "run sorted", r);
+            if (s == LEY_OK && !hp.order(st, hp.gth)) s = LEY_ECUDA;
+            if (s == LEY_OK) s = stream_out(ra, w.perm, 0, rn, hs + r0 * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+            hp.mark(hp.gth, "run gathered", r);
+            hp.mark(hp.d2h, "run out end", r);
+            if (s == LEY_OK && !(buf_free[b] = hp.record(hp.gth))) s = LEY_ECUDA;
             runs.push_back({hs + r0 * a.rec, rn});
         }
         // --- merge: the runs must be complete in host memory before they are cut
         if (s == LEY_OK && cudaStreamSynchronize(hp.d2h) != cudaSuccess) s = LEY_ECUDA;
         std::vector<std::vector<ull>> cuts;
+        const auto t_plan = std::chrono::steady_clock::now();
         if (s == LEY_OK) cuts = plan_partitions(runs, a.n, r_len, a.rec, a.kb);
+        hp.mark(st, "partitions planned");
+        if (hp.trace)
+            std::fprintf(stderr, "leysort trace plan_partitions %.3f ms on the host\n",
+                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count());
         if (dbg) std::fprintf(stderr, "leysort: runs formed (status %d), %zu merge partitions\n",
                               (int)s, cuts.empty() ? (size_t)0 : cuts.size() - 1);
-        std::vector<ull> off_host((size_t)(k + 1) * (cuts.size() + 1));
+        std::vector<ull> off(k + 1);
         ull out_pos = 0;
         for (size_t p = 0; p + 1 < cuts.size() && s == LEY_OK; p++) {
             const int b = p & 1;
-            ull* off = &off_host[p * (k + 1)];
             off[0] = 0;
             for (uint32_t i = 0; i < k; i++) off[i + 1] = off[i] + (cuts[p + 1][i] - cuts[p][i]);
             const ull m = off[k];
@@ -728,29 +834,32 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
                 s = LEY_ENOMEM;
                 break;
             }
-            if (buf_free[b] && cudaStreamWaitEvent(hp.h2d, buf_free[b], 0) != cudaSuccess) s = LEY_ECUDA;
+            if (m == 0) continue;
+            if (!hp.wait(hp.h2d, buf_free[b]) || !hp.wait(st, buf_free[b])) s = LEY_ECUDA;
+            hp.mark(hp.h2d, "part in begin", (long)p);
             for (uint32_t i = 0; i < k && s == LEY_OK; i++) {
                 const ull len = cuts[p + 1][i] - cuts[p][i];
                 if (len && cudaMemcpyAsync(dbuf[b] + off[i] * a.rec, runs[i].base + cuts[p][i] * a.rec,
                                            len * a.rec, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
                     s = LEY_ECUDA;
             }
+            hp.mark(hp.h2d, "part in end", (long)p);
             if (s == LEY_OK && !hp.order(hp.h2d, st)) s = LEY_ECUDA;
-            if (m == 0) continue;
-            Work w = make_work(ws, L, m, ds->err);
+            Work w = make_work(ws[b], L, m, ds->err);
             SortArgs ma = a;
             ma.in = dbuf[b];
             ma.n = m;
-            if (s == LEY_OK) s = stage_merge(ma, dbuf[b], off, off_dev, k, w, L, st, ds->sms);
-            if (s == LEY_OK) s = stream_out(ma, w.perm, 0, m, a.out + out_pos * a.rec, stg, q, st, hp, stg_free, ds->sms);
-            if (s == LEY_OK) {
-                buf_free[b] = hp.ev();
-                if (!buf_free[b] || cudaEventRecord(buf_free[b], st) != cudaSuccess) s = LEY_ECUDA;
-            }
+            if (s == LEY_OK) s = stage_merge(ma, dbuf[b], off.data(), off_dev, k, w, L, st, ds->sms);
+            hp.mark(st, "part merged", (long)p);
+            if (s == LEY_OK && !hp.order(st, hp.gth)) s = LEY_ECUDA;
+            if (s == LEY_OK) s = stream_out(ma, w.perm, 0, m, a.out + out_pos * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+            hp.mark(hp.gth, "part gathered", (long)p);
+            hp.mark(hp.d2h, "part out end", (long)p);
+            if (s == LEY_OK && !(buf_free[b] = hp.record(hp.gth))) s = LEY_ECUDA;
             out_pos += m;
-            // off_host slot p is read by the copy above; keep it until the end
         }
         if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
+        if (!hp.order(hp.gth, st) && s == LEY_OK) s = LEY_ECUDA;
         cudaFreeAsync(dmem, st);
         if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
     }
@@ -900,10 +1009,7 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
     const Layout L = make_layout(n, true);
     const size_t total = L.total + align_up(sizeof(ull) * (k + 1), 256);
     void* base = nullptr;
-    if (cudaMallocAsync(&base, total, st) != cudaSuccess) {
-        cudaGetLastError();
-        return LEY_ENOMEM;
-    }
+    if (!scratch_alloc(ds, &base, total, st)) return LEY_ENOMEM;
     SortArgs a{};
     a.mode = MODE_RECORDS;
     a.in = static_cast<const uint8_t*>(runs);
@@ -916,7 +1022,6 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
     ley_status s = stage_merge(a, a.in, off.data(), off_dev, k, w, L, st, ds->sms);
     if (s == LEY_OK) s = stage_gather(a, w.perm, st, ds->sms, 0, n, a.out);
     cudaFreeAsync(base, st);
-    // off is pageable host memory: its copy completed before cudaMemcpyAsync returned
     return s;
 }
 
@@ -927,6 +1032,19 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
         rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     *bytes = n ? make_layout(n, !fused_gather(rec_bytes)).total : 0;
+    return LEY_OK;
+}
+
+ley_status ley_release_cache(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_host_scratch_mu);
+        if (g_host_scratch && cudaFreeHost(g_host_scratch) != cudaSuccess) return LEY_ECUDA;
+        g_host_scratch = nullptr;
+        g_host_scratch_bytes = 0;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& d : g_dev)
+        if (d.init && d.pool && cudaMemPoolTrimTo(d.pool, 0) != cudaSuccess) return LEY_ECUDA;
     return LEY_OK;
 }
 

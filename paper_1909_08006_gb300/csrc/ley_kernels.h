@@ -51,6 +51,11 @@ cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsign
 cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
                                const unsigned long long* off_dev, uint32_t k, uint32_t lo_mask);
 cudaError_t launch_halve_offsets(cudaStream_t s, unsigned long long* off, uint32_t runs);
+// dst[0, count) = host[0, count), count <= kMaxOffsets, stream-ordered on s
+// (the values travel in the kernel's parameters).
+constexpr int kMaxOffsets = 129;  // k + 1 offsets of at most 128 runs
+cudaError_t launch_set_offsets(cudaStream_t s, unsigned long long* dst,
+                               const unsigned long long* host, uint32_t count);
 cudaError_t launch_tuple_index(cudaStream_t s, int grid, const uint4* t, uint32_t* perm,
                                unsigned long long n);
 

@@ -124,6 +124,24 @@ cudaError_t launch_halve_offsets(cudaStream_t s, ull* off, uint32_t runs) {
     return cudaGetLastError();
 }
 
+// Writes up to kMaxOffsets run offsets, passed by value in the kernel's
+// parameters (so the host needs no pinned copy buffer), to dst.
+struct OffsetBlock {
+    ull v[kMaxOffsets];
+};
+
+__global__ void k_set_offsets(ull* dst, OffsetBlock b, uint32_t count) {
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = b.v[i];
+}
+
+cudaError_t launch_set_offsets(cudaStream_t s, ull* dst, const ull* host, uint32_t count) {
+    if (count > (uint32_t)kMaxOffsets) return cudaErrorInvalidValue;
+    OffsetBlock b;
+    for (uint32_t i = 0; i < count; i++) b.v[i] = host[i];
+    k_set_offsets<<<1, 128, 0, s>>>(dst, b, count);
+    return cudaGetLastError();
+}
+
 // Copies the tuples' input positions (the w field) out as the permutation.
 __global__ void k_tuple_index(const uint4* __restrict__ t, uint32_t* __restrict__ perm, ull n) {
     for (ull i = (ull)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (ull)gridDim.x * blockDim.x)

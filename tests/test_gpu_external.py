@@ -64,6 +64,20 @@ def test_partial_sort_exact(orc, ley, n):
     assert np.array_equal(got, orc.sort_records(rec.numpy()))
 
 
+def test_release_cache_between_sorts(orc, ley):
+    # the device pool and the pinned run scratch are returned, then rebuilt
+    rec = datagen.uniform_records(120_000, seed=21)
+    want = orc.sort_records(rec.numpy())
+    assert np.array_equal(host_sort(ley, rec, 6 << 20), want)
+    torch.cuda.synchronize()
+    ley.ley_release_cache()
+    assert np.array_equal(host_sort(ley, rec, 6 << 20), want)
+    d_in = rec.to("cuda:0")
+    d_out = torch.empty_like(d_in)
+    ley.ley_sort_records(d_in, d_out)
+    assert np.array_equal(d_out.cpu().numpy(), want)
+
+
 def test_external_budget_too_small(ley):
     rec = datagen.uniform_records(50_000, seed=1)
     with pytest.raises(ley.LeyError) as e:
