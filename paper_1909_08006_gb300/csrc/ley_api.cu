@@ -404,9 +404,12 @@ struct HostPipe {
     std::vector<cudaEvent_t> evs;
     bool ok = true;
     explicit HostPipe(cudaStream_t st) {
+        // the gathers feed the writer: their kernels go first when SMs free up
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
         ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
              cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&gth, cudaStreamNonBlocking) == cudaSuccess;
+             cudaStreamCreateWithPriority(&gth, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
         if (ok) {
             cudaEvent_t e = ev();  // side streams start after the caller's prior work
             ok = e && cudaEventRecord(e, st) == cudaSuccess &&
@@ -476,14 +479,18 @@ struct HostPipe {
     }
 };
 
-// Streams sorted records to host memory: perm[j0, j1) gathered into two
-// alternating device staging buffers of q records on `st`, each copied to
-// host_out + (j - j0) records on the writer stream as soon as it is full.
+// Streams sorted records to host memory: perm[j0, j1) gathered into
+// kStaging rotating device staging buffers of q records on `st`, each copied
+// to host_out + (j - j0) records on the writer stream as soon as it is full.
+// Several buffers let the gathers run ahead of the copies, so a gather
+// delayed behind other kernels does not stall the writer.
+constexpr int kStaging = 4;
 static ley_status stream_out(const SortArgs& a, const uint32_t* perm, ull j0, ull j1,
-                             uint8_t* host_out, uint8_t* const stg[2], ull q, cudaStream_t st,
-                             HostPipe& hp, cudaEvent_t stg_free[2], int sms) {
+                             uint8_t* host_out, uint8_t* const stg[kStaging], ull q,
+                             cudaStream_t st, HostPipe& hp, cudaEvent_t stg_free[kStaging],
+                             int sms) {
     int b = 0;
-    for (ull j = j0; j < j1; j += q, b ^= 1) {
+    for (ull j = j0; j < j1; j += q, b = (b + 1) % kStaging) {
         const ull je = j + q < j1 ? j + q : j1;
         if (stg_free[b] && cudaStreamWaitEvent(st, stg_free[b], 0) != cudaSuccess) return LEY_ECUDA;
         ley_status s = stage_gather(a, perm, st, sms, j, je, stg[b]);
@@ -518,8 +525,8 @@ static ley_status stream_in_extract(const SortArgs& a, const uint8_t* host_in, u
 
 static ull staging_records(ull n, uint32_t rec, ull budget) {
     ull q = (64ull << 20) / rec;  // 64 MB staging buffers
-    if (budget) {
-        const ull cap = budget / (16ull * rec);
+    if (budget) {  // all kStaging buffers together take at most budget / 8
+        const ull cap = budget / (8ull * kStaging * rec);
         if (cap < q) q = cap;
     }
     if (q < 1024) q = 1024;
@@ -538,14 +545,14 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
     const Layout L = make_layout(a.n, true);
     const ull q = staging_records(a.n, a.rec, budget);
     const size_t stg_bytes = align_up(q * a.rec, 256);
-    const size_t need = align_up(bytes, 256) + L.total + 2 * stg_bytes;
+    const size_t need = align_up(bytes, 256) + L.total + kStaging * stg_bytes;
     if (budget && need > budget) return LEY_ENOMEM;
     void* dmem = nullptr;
     if (!scratch_alloc(ds, &dmem, need, st)) return LEY_ENOMEM;
     char* din = static_cast<char*>(dmem);
     char* ws = din + align_up(bytes, 256);
-    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
-                       reinterpret_cast<uint8_t*>(ws + L.total + stg_bytes)};
+    uint8_t* stg[kStaging];
+    for (int i = 0; i < kStaging; i++) stg[i] = reinterpret_cast<uint8_t*>(ws + L.total + i * stg_bytes);
     ley_status s = LEY_OK;
     {
         HostPipe hp(st);
@@ -561,7 +568,7 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         hp.mark(st, "extracted");
         if (s == LEY_OK) s = stage_levels_finish(d, w, ks, st, ds->sms);
         hp.mark(st, "sorted");
-        cudaEvent_t stg_free[2] = {nullptr, nullptr};
+        cudaEvent_t stg_free[kStaging] = {};
         if (s == LEY_OK) s = stream_out(d, w.perm, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
         hp.mark(st, "gathered");
         hp.mark(hp.d2h, "out end");
@@ -728,12 +735,13 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
 // the gather stream that the writer stream copies into pinned host scratch.
 // Merge: the output is cut into partitions by k-way co-rank; each partition's
 // slices of every run are copied in, merged by merge path, gathered and
-// streamed to `out`.  Two record buffers and two workspaces alternate, so one
-// run (or partition) streams out while the next is copied in and sorted, and
-// runs are about n / kExtRuns records, so that filling and draining this
-// pipeline (the first copy in, the last copy out) costs little next to the
-// copies themselves.
+// streamed to `out`.  kExtBufs record buffers and workspaces rotate, so that
+// while one run (or partition) streams out, the next is sorted and the one
+// after it is already being copied in; runs are about n / kExtRuns records,
+// so that filling and draining this pipeline (the first copy in, the last
+// copy out) costs little next to the copies themselves.
 constexpr ull kExtRuns = 16;
+constexpr int kExtBufs = 3;
 constexpr ull kExtMinRun = 4ull << 20;
 
 static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t st) {
@@ -741,11 +749,11 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     if (!ds) return LEY_ECUDA;
     const ull q = staging_records(a.n, a.rec, budget);
     const size_t stg_bytes = align_up(q * a.rec, 256);
-    const size_t fixed = 2 * stg_bytes + 64 * 1024;
+    const size_t fixed = kStaging * stg_bytes + 64 * 1024;
     if (budget <= fixed) return LEY_ENOMEM;
-    // largest run (whole tiles) whose two record buffers and two workspaces fit
+    // largest run (whole tiles) whose record buffers and workspaces fit
     auto need = [&](ull r) {
-        return 2 * align_up(r * a.rec, 256) + 2 * make_layout(r, true).total + fixed;
+        return kExtBufs * (align_up(r * a.rec, 256) + make_layout(r, true).total) + fixed;
     };
     ull lo = 0, hi = a.n / kPassTile + 1;
     while (lo < hi) {
@@ -762,7 +770,7 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     if (k > 128) return LEY_ENOMEM;  // budget too small for the merge fan-in
     const Layout L = make_layout(r_len, true);
     const size_t in_bytes = align_up(r_len * a.rec, 256);
-    const size_t total = 2 * in_bytes + 2 * L.total + 2 * stg_bytes + 8 * 1024;
+    const size_t total = kExtBufs * (in_bytes + L.total) + kStaging * stg_bytes + 8 * 1024;
     const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
     if (dbg)
         std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
@@ -774,26 +782,31 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     void* dmem = nullptr;
     if (!scratch_alloc(ds, &dmem, total, st)) return LEY_ENOMEM;
     char* base = static_cast<char*>(dmem);
-    uint8_t* dbuf[2] = {reinterpret_cast<uint8_t*>(base), reinterpret_cast<uint8_t*>(base + in_bytes)};
-    char* ws[2] = {base + 2 * in_bytes, base + 2 * in_bytes + L.total};
-    char* tail = base + 2 * in_bytes + 2 * L.total;
-    uint8_t* stg[2] = {reinterpret_cast<uint8_t*>(tail), reinterpret_cast<uint8_t*>(tail + stg_bytes)};
-    ull* off_dev = reinterpret_cast<ull*>(tail + 2 * stg_bytes);
+    uint8_t* dbuf[kExtBufs];
+    char* ws[kExtBufs];
+    for (int i = 0; i < kExtBufs; i++) {
+        dbuf[i] = reinterpret_cast<uint8_t*>(base + i * in_bytes);
+        ws[i] = base + kExtBufs * in_bytes + i * L.total;
+    }
+    char* tail = base + kExtBufs * (in_bytes + L.total);
+    uint8_t* stg[kStaging];
+    for (int i = 0; i < kStaging; i++) stg[i] = reinterpret_cast<uint8_t*>(tail + i * stg_bytes);
+    ull* off_dev = reinterpret_cast<ull*>(tail + kStaging * stg_bytes);
     ley_status s = LEY_OK;
     {
         HostPipe hp(st);
         if (!hp.ok) s = LEY_ECUDA;
         const KeySpec ks = record_keyspec(a.kb);
-        cudaEvent_t stg_free[2] = {nullptr, nullptr};
+        cudaEvent_t stg_free[kStaging] = {};
         // buffer b and workspace b are free again once the gathers that read
-        // them (two runs or partitions back) are done
-        cudaEvent_t buf_free[2] = {nullptr, nullptr};
+        // them (kExtBufs runs or partitions back) are done
+        cudaEvent_t buf_free[kExtBufs] = {};
         // --- run formation
         std::vector<HostRun> runs;
         for (uint32_t r = 0; r < k && s == LEY_OK; r++) {
             const ull r0 = (ull)r * r_len;
             const ull rn = a.n - r0 < r_len ? a.n - r0 : r_len;
-            const int b = r & 1;
+            const int b = (int)(r % kExtBufs);
             if (!hp.wait(hp.h2d, buf_free[b]) || !hp.wait(st, buf_free[b])) s = LEY_ECUDA;
             SortArgs ra = a;
             ra.in = dbuf[b];
@@ -826,7 +839,7 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
         std::vector<ull> off(k + 1);
         ull out_pos = 0;
         for (size_t p = 0; p + 1 < cuts.size() && s == LEY_OK; p++) {
-            const int b = p & 1;
+            const int b = (int)(p % kExtBufs);
             off[0] = 0;
             for (uint32_t i = 0; i < k; i++) off[i + 1] = off[i] + (cuts[p + 1][i] - cuts[p][i]);
             const ull m = off[k];
