@@ -376,6 +376,45 @@ def host_free(a):
     _libcuda().cuMemFreeHost(p)
 
 
+def link_peaks(dev, nbytes=2 << 30, reps=3):
+    """Host<->device copy rates of this machine, measured now with the same kind
+    of host memory as the sort's buffers: H2D alone, D2H alone, and both
+    directions at once (GB/s each way)."""
+    import ctypes
+    import torch
+    cu = _libcuda()
+    cu.cuMemcpyHtoDAsync_v2.argtypes = [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_void_p]
+    cu.cuMemcpyDtoHAsync_v2.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t,
+                                        ctypes.c_void_p]
+    h1, h2 = host_alloc(nbytes), host_alloc(nbytes)
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def h2d():
+        assert cu.cuMemcpyHtoDAsync_v2(d1.data_ptr(), h1.ctypes.data, nbytes, s1.cuda_stream) == 0
+
+    def d2h():
+        assert cu.cuMemcpyDtoHAsync_v2(h2.ctypes.data, d2.data_ptr(), nbytes, s2.cuda_stream) == 0
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / reps
+
+    r = {"h2d_GBps": nbytes / timed(h2d) / 1e9, "d2h_GBps": nbytes / timed(d2h) / 1e9,
+         "duplex_each_GBps": nbytes / timed(lambda: (h2d(), d2h())) / 1e9}
+    del d1, d2
+    host_free(h1)
+    host_free(h2)
+    return {k: round(v, 1) for k, v in r.items()}
+
+
 def run_host_mode(args, world, rank, dev, stream, pg):
     """Records in pinned host memory, sorted to pinned host memory under a
     device budget: the partially in-memory sort (input resident on the device)
@@ -408,6 +447,21 @@ def run_host_mode(args, world, rank, dev, stream, pg):
     host_free(h_in_np)
     host_free(h_out_np)
     link = 2 * n * REC if mode == "partial" else 4 * n * REC
+    lp = link_peaks(dev)
+    if mode == "partial":
+        # the copy in and the copy out cannot overlap (the gather needs the
+        # finished order): floor = n*100/h2d + n*100/d2h
+        floor_s = n * REC / (lp["h2d_GBps"] * 1e9) + n * REC / (lp["d2h_GBps"] * 1e9)
+        roof = {"bound": "link", "achieved": round(link / dt / 1e9, 1),
+                "peak": round(link / floor_s / 1e9, 1), "unit": "GB/s",
+                "frac": round(floor_s / dt, 4), "peak_source": "measured in this run (serial H2D + D2H)"}
+    else:
+        # runs in and out, then partitions in and out: 2*n*100 bytes each
+        # way, the two directions overlapped
+        each = 2 * n * REC / dt / 1e9
+        roof = {"bound": "link", "achieved": round(each, 1), "peak": lp["duplex_each_GBps"],
+                "unit": "GB/s each way", "frac": round(each / lp["duplex_each_GBps"], 4),
+                "peak_source": "measured in this run (full duplex)"}
     return {
         "metric": f"GB/s of 100-byte records sorted host-to-host ({mode}, device budget)",
         "value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s", "n_gpus": world,
@@ -416,7 +470,7 @@ def run_host_mode(args, world, rank, dev, stream, pg):
         "data": "synthetic", "config": {"workload": f"{args.workload}_{n}", "records": n,
                                         "budget_bytes": budget, "mode": mode,
                                         "link_bytes_per_step": link},
-        "link_GBps": round(link / dt / 1e9, 2),
+        "link_GBps": round(link / dt / 1e9, 2), "roofline": roof, "link_peaks": lp,
     }
 
 

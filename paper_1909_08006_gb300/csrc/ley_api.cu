@@ -95,6 +95,14 @@ uint32_t* device_err_word() {
     return s ? s->err : nullptr;
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("LEY_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 // ------------------------------------------------------------- profiling
 
 struct PendingEv {

@@ -35,6 +35,15 @@ __device__ unsigned long long g_ley_phase[64];
 
 // ------------------------------------------------------------- helpers
 
+// Programmatic dependent launch: the level kernels are launched so that the
+// next one may be scheduled while this one runs; each first waits for its
+// predecessor's completion and memory (a no-op when launched plainly), then
+// lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t bswap32(uint32_t v) { return __byte_perm(v, 0, 0x0123); }
 
 // Key byte d of a tuple (d in 0..11).
@@ -298,6 +307,7 @@ __global__ void __launch_bounds__(kHistThreads)
 k_hist(Work w, KeySpec ks, int L) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
+    pdl_enter();
     const int p = L & 1;
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
@@ -369,6 +379,7 @@ k_scan(Work w, int L) {
     __shared__ uint8_t sh_head[kScanChunk];
     __shared__ uint8_t sh_last[kScanChunk];
     __shared__ uint32_t sh_chunk;
+    pdl_enter();
     const int p = L & 1;
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
@@ -520,6 +531,7 @@ k_classify(Work w, KeySpec ks, int L) {
     __shared__ uint32_t sh_cnt[4][kRadix];   // per warp: bin counts
     __shared__ uint32_t sh_gs[4][kRadix];    // per warp: task start offsets
     __shared__ uint32_t sh_gc[4][kRadix];    // per warp: count << 1 | single-bucket
+    pdl_enter();
     const int p = L & 1, lane = threadIdx.x & 31;
     const ull packed = w.ctl->lvl[L].big_packed;
     const uint32_t nseg = (uint32_t)(packed >> kPackShift);
@@ -733,6 +745,7 @@ k_pass(Work w, KeySpec ks, int L) {
     __shared__ uint32_t loc_off[kRadix];
     __shared__ ull gbase[kRadix];
     __shared__ uint32_t scan_tot[kRadix / 32];
+    pdl_enter();
 
     const int p = L & 1;
     const ull packed = w.ctl->lvl[L].big_packed;
@@ -1293,6 +1306,7 @@ __global__ void __launch_bounds__(kFinThreads, 4)
 k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     extern __shared__ uint4 B[];  // kSmall tuples
     __shared__ FinShared S;
+    pdl_enter();
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
     __shared__ __align__(8) uint64_t gbar;  // MODE 2: the record windows' bulk copies
@@ -1450,18 +1464,15 @@ cudaError_t launch_init(cudaStream_t s, const Work& w, ull n, int digit0) {
 }
 
 cudaError_t launch_hist(const LaunchCfg& c, const Work& w, KeySpec ks, int level) {
-    k_hist<<<c.grid, kHistThreads, 0, c.stream>>>(w, ks, level);
-    return cudaGetLastError();
+    return launch_pdl(k_hist, c.grid, kHistThreads, 0, c.stream, w, ks, level);
 }
 
 cudaError_t launch_scan(const LaunchCfg& c, const Work& w, int level) {
-    k_scan<<<c.grid, kRadix, 0, c.stream>>>(w, level);
-    return cudaGetLastError();
+    return launch_pdl(k_scan, c.grid, kRadix, 0, c.stream, w, level);
 }
 
 cudaError_t launch_classify(const LaunchCfg& c, const Work& w, KeySpec ks, int level) {
-    k_classify<<<c.grid, 128, 0, c.stream>>>(w, ks, level);
-    return cudaGetLastError();
+    return launch_pdl(k_classify, c.grid, 128, 0, c.stream, w, ks, level);
 }
 
 cudaError_t launch_classify_partition(cudaStream_t s, const Work& w) {
@@ -1470,15 +1481,13 @@ cudaError_t launch_classify_partition(cudaStream_t s, const Work& w) {
 }
 
 cudaError_t launch_pass(const LaunchCfg& c, const Work& w, KeySpec ks, int level) {
-    k_pass<<<c.grid, kPassThreads, c.smem, c.stream>>>(w, ks, level);
-    return cudaGetLastError();
+    return launch_pdl(k_pass, c.grid, kPassThreads, c.smem, c.stream, w, ks, level);
 }
 
 cudaError_t launch_finish_records(const LaunchCfg& c, const Work& w, KeySpec ks) {
     Emitter<0> e;
     e.perm = w.perm;
-    k_finish<0><<<c.grid, kFinThreads, c.smem, c.stream>>>(w, ks, e);
-    return cudaGetLastError();
+    return launch_pdl(k_finish<0>, c.grid, kFinThreads, c.smem, c.stream, w, ks, e);
 }
 
 cudaError_t launch_finish_gather(const LaunchCfg& c, const Work& w, KeySpec ks, const uint8_t* in,
@@ -1487,8 +1496,7 @@ cudaError_t launch_finish_gather(const LaunchCfg& c, const Work& w, KeySpec ks, 
     e.in = in;
     e.out = out;
     e.n_in = n_in;
-    k_finish<2><<<c.grid, kFinThreads, c.smem, c.stream>>>(w, ks, e);
-    return cudaGetLastError();
+    return launch_pdl(k_finish<2>, c.grid, kFinThreads, c.smem, c.stream, w, ks, e);
 }
 
 cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, uint64_t* keys_out,
@@ -1496,8 +1504,7 @@ cudaError_t launch_finish_pairs(const LaunchCfg& c, const Work& w, KeySpec ks, u
     Emitter<1> e;
     e.keys = keys_out;
     e.idx = idx_out;
-    k_finish<1><<<c.grid, kFinThreads, c.smem, c.stream>>>(w, ks, e);
-    return cudaGetLastError();
+    return launch_pdl(k_finish<1>, c.grid, kFinThreads, c.smem, c.stream, w, ks, e);
 }
 
 cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, ull n,
