@@ -89,6 +89,46 @@ ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
                                uint64_t mem_budget, ley_stream_t stream);
 
 /*
+ * Batched sorts: many independent requests of uneven sizes sorted by one
+ * sequence of launches, each request exactly as its own ley_sort_records /
+ * ley_sort_keys_index call would sort it.  (The paper sorts one data set; a
+ * batch is this library's form of many small sorts, the requests being the
+ * top-level buckets of one MSD sort -- Algorithm 1 never moves a tuple out
+ * of its bucket.)
+ *
+ *   reqs[count]  host array, read before the call returns; requests with
+ *                n == 0 are skipped.  All buffers on the device, as for the
+ *                single-request call (records 16-byte aligned; keys 8, payloads
+ *                4); a request's outputs must not overlap its inputs, and no
+ *                request's buffers may overlap another request's outputs.
+ *   sum over requests of n rounded up to 4096 must be < 2^32.
+ * Asynchronous on `stream`; scratch (about 36 B per record slot, plus 4 B for
+ * record sizes other than 100) counts against mem_budget.  The call does no
+ * host synchronisation and no pageable copies, so it can be captured in a
+ * CUDA graph (the request array is copied into the launches' parameters).
+ */
+typedef struct {
+    const void* in;  /* n * rec_bytes bytes */
+    void* out;       /* n * rec_bytes bytes */
+    uint64_t n;
+} ley_records_request;
+
+ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t count,
+                                  uint32_t rec_bytes, uint32_t key_bytes, uint64_t mem_budget,
+                                  ley_stream_t stream);
+
+typedef struct {
+    const uint64_t* keys_in;
+    const uint32_t* idx_in;
+    uint64_t* keys_out;
+    uint32_t* idx_out;
+    uint64_t n;
+} ley_pairs_request;
+
+ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t count,
+                                     uint64_t mem_budget, ley_stream_t stream);
+
+/*
  * One round of Algorithm 1 (Section 3.1, "Cache Aware Scattering Process"):
  * the histogram of key byte `digit` and the stable partition of the records
  * into the 256 buckets of that byte.

@@ -23,6 +23,7 @@ __all__ = [
     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
     "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS", "ley_merge_records",
+    "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -38,6 +39,16 @@ class LeyError(RuntimeError):
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64),
                 ("total_ms", ctypes.c_double)]
+
+
+class _RecordsReq(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class _PairsReq(ctypes.Structure):
+    _fields_ = [("keys_in", ctypes.c_void_p), ("idx_in", ctypes.c_void_p),
+                ("keys_out", ctypes.c_void_p), ("idx_out", ctypes.c_void_p),
+                ("n", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -79,6 +90,10 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_records_noalloc.restype = ctypes.c_int
     lib.ley_release_cache.argtypes = []
     lib.ley_release_cache.restype = ctypes.c_int
+    lib.ley_sort_records_batch.argtypes = [ctypes.POINTER(_RecordsReq), u32, u32, u32, u64, vp]
+    lib.ley_sort_records_batch.restype = ctypes.c_int
+    lib.ley_sort_keys_index_batch.argtypes = [ctypes.POINTER(_PairsReq), u32, u64, vp]
+    lib.ley_sort_keys_index_batch.restype = ctypes.c_int
     return lib
 
 
@@ -142,6 +157,43 @@ def ley_sort_records(inp, out, n: int | None = None, rec_bytes: int | None = Non
     st = _lib.ley_sort_records(_addr(inp), _addr(out), n, rec_bytes, key_bytes, mem_budget,
                                _stream(stream, inp, out))
     return _check(st, "ley_sort_records")
+
+
+def ley_sort_records_batch(requests, rec_bytes: int = 100, key_bytes: int = 10,
+                           mem_budget: int = 0, stream=None) -> int:
+    """Sort many record arrays at once, each as ley_sort_records would.
+    ``requests`` holds (in, out) pairs of device uint8 [n, rec_bytes] tensors,
+    or (in, out, n) with addresses."""
+    arr = (_RecordsReq * max(1, len(requests)))()
+    st = None
+    for i, rq in enumerate(requests):
+        inp, out = rq[0], rq[1]
+        n = int(rq[2]) if len(rq) > 2 else int(inp.shape[0])
+        arr[i] = _RecordsReq(_addr(inp), _addr(out), n)
+        if st is None and hasattr(inp, "is_cuda"):
+            st = _stream(stream, inp)
+    if st is None:
+        st = _stream(stream)
+    return _check(_lib.ley_sort_records_batch(arr, len(requests), rec_bytes, key_bytes,
+                                              mem_budget, st), "ley_sort_records_batch")
+
+
+def ley_sort_keys_index_batch(requests, mem_budget: int = 0, stream=None) -> int:
+    """Sort many (key, payload) arrays at once, each as ley_sort_keys_index
+    would.  ``requests`` holds (keys_in, idx_in, keys_out, idx_out) tuples of
+    device tensors, or the same with a count appended and addresses."""
+    arr = (_PairsReq * max(1, len(requests)))()
+    st = None
+    for i, rq in enumerate(requests):
+        ki, ii, ko, io = rq[:4]
+        n = int(rq[4]) if len(rq) > 4 else int(ki.shape[0])
+        arr[i] = _PairsReq(_addr(ki), _addr(ii), _addr(ko), _addr(io), n)
+        if st is None and hasattr(ki, "is_cuda"):
+            st = _stream(stream, ki)
+    if st is None:
+        st = _stream(stream)
+    return _check(_lib.ley_sort_keys_index_batch(arr, len(requests), mem_budget, st),
+                  "ley_sort_keys_index_batch")
 
 
 def ley_sort_records_noalloc(inp, out, n: int | None = None, rec_bytes: int | None = None,

@@ -308,8 +308,7 @@ static ley_status stage_extract_records(const SortArgs& a, const Work& w, const 
 
 // The MSD levels (histogram, offset scan, classify, scatter) and the
 // small-bucket finish; records mode leaves the permutation in w.perm.
-static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const KeySpec& ks,
-                                      cudaStream_t st, int sms, bool fuse = false) {
+static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st, int sms) {
     const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
@@ -320,6 +319,13 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
         LEY_TRY(launch("classify", st, [&] { return launch_classify(cc, w, ks, lvl); }));
         LEY_TRY(launch("pass", st, [&] { return launch_pass(cp, w, ks, lvl); }));
     }
+    return LEY_OK;
+}
+
+static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const KeySpec& ks,
+                                      cudaStream_t st, int sms, bool fuse = false) {
+    ley_status s0 = stage_levels(w, ks, st, sms);
+    if (s0 != LEY_OK) return s0;
     if (a.mode == MODE_PAIRS) {
         LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_PAIRS), kFinThreads,
                      kernel_smem(KK_FINISH_PAIRS), st};
@@ -388,6 +394,69 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
     s = stage_levels_finish(a, w, ks, st, sms, fuse);
     if (s != LEY_OK || a.mode == MODE_PAIRS || fuse) return s;
     return stage_gather(a, w.perm, st, sms, 0, a.n, a.out);
+}
+
+// ------------------------------------------------------- batched sorts
+
+// Sorts the requests of a batch (non-empty, offsets assigned, npos = end of
+// the last request's tiles) as one sort over R top-level segments.
+static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_t rec,
+                            uint32_t kb, bool pairs, ull budget, cudaStream_t st) {
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    const uint32_t R = (uint32_t)reqs.size();
+    const bool fuse = !pairs && rec == 100;
+    const Layout L = make_layout(npos, !pairs && !fuse);
+    const uint32_t ntiles = (uint32_t)(npos / kPassTile);
+    const size_t rq_bytes = align_up(R * sizeof(BatchReq), 256);
+    const size_t tr_bytes = align_up((size_t)ntiles * sizeof(uint32_t), 256);
+    const size_t total = L.total + rq_bytes + tr_bytes;
+    if (budget && total > budget) return LEY_ENOMEM;
+    if (R > L.cap_seg) return LEY_EUNSUPPORTED;  // cannot happen: each request has a tile
+    void* base = nullptr;
+    if (!scratch_alloc(ds, &base, total, st)) return LEY_ENOMEM;
+    char* b = static_cast<char*>(base);
+    Work w = make_work(b, L, npos, ds->err);
+    BatchReq* dreqs = reinterpret_cast<BatchReq*>(b + L.total);
+    uint32_t* tile_req = reinterpret_cast<uint32_t*>(b + L.total + rq_bytes);
+    const KeySpec ks = pairs ? pair_keyspec() : record_keyspec(kb);
+    const int sms = ds->sms;
+    ley_status s = LEY_OK;
+    auto run = [&]() -> ley_status {
+        LEY_TRY(launch("upload", st, [&] {
+            return launch_upload(st, dreqs, reqs.data(), R * sizeof(BatchReq));
+        }));
+        ley_status t = stage_prepare(w, L, st, npos, 0);
+        if (t != LEY_OK) return t;
+        LEY_TRY(launch("batch_setup", st, [&] {
+            return launch_batch_setup(st, dreqs, R, w, tile_req, ntiles, 0);
+        }));
+        LaunchCfg c{sms * blocks_per_sm(pairs ? KK_EXTRACT_PAIRS : KK_EXTRACT_REC), 256, 0, st};
+        LEY_TRY(launch("extract", st, [&] {
+            return pairs ? launch_batch_extract_pairs(c, dreqs, tile_req, ntiles, w)
+                         : launch_batch_extract_records(c, dreqs, tile_req, ntiles, rec, ks, w);
+        }));
+        t = stage_levels(w, ks, st, sms);
+        if (t != LEY_OK) return t;
+        if (pairs || fuse) {
+            const KernelKind fk = pairs ? KK_FINISH_PAIRS : KK_FINISH_GATHER;
+            LaunchCfg cf{sms * blocks_per_sm(fk), kFinThreads, kernel_smem(fk), st};
+            LEY_TRY(launch("finish_gather", st, [&] {
+                return launch_batch_finish(cf, w, ks, dreqs, tile_req, pairs);
+            }));
+            return LEY_OK;
+        }
+        LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+        LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
+        LEY_TRY(launch("gather", st, [&] {
+            return launch_batch_gather_generic(st, sms * blocks_per_sm(KK_GATHER_GENERIC), dreqs,
+                                               tile_req, w.perm, npos, rec, w.err);
+        }));
+        return LEY_OK;
+    };
+    s = run();
+    cudaFreeAsync(base, st);
+    return s;
 }
 
 static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st) {
@@ -973,6 +1042,79 @@ ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
     a.n = n;
     a.kb = 8;
     return run_device_sort(a, mem_budget, static_cast<cudaStream_t>(stream));
+}
+
+ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t count,
+                                  uint32_t rec_bytes, uint32_t key_bytes, uint64_t mem_budget,
+                                  ley_stream_t stream) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u))
+        return LEY_EUNSUPPORTED;
+    if (count == 0) return LEY_OK;
+    if (!reqs) return LEY_EINVAL;
+    std::vector<BatchReq> v;
+    v.reserve(count);
+    ull npos = 0;
+    for (uint32_t r = 0; r < count; r++) {
+        const ley_records_request& q = reqs[r];
+        if (q.n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+        if (q.n == 0) continue;
+        if (!q.in || !q.out) return LEY_EINVAL;
+        const ull bytes = q.n * rec_bytes;
+        if (overlaps(q.in, bytes, q.out, bytes)) return LEY_EINVAL;
+        if (!aligned16(q.in) || !aligned16(q.out)) return LEY_EINVAL;
+        if (mem_kind(q.in) != MK_DEVICE || mem_kind(q.out) != MK_DEVICE) return LEY_EINVAL;
+        BatchReq b{};
+        b.in = static_cast<const uint8_t*>(q.in);
+        b.out = static_cast<uint8_t*>(q.out);
+        b.n = q.n;
+        b.off = npos;
+        npos += (ull)ceil_div_u64(q.n, kPassTile) * kPassTile;
+        v.push_back(b);
+    }
+    if (v.empty()) return LEY_OK;
+    if (npos >= (1ull << 32)) return LEY_EUNSUPPORTED;
+    return run_batch(v, npos, rec_bytes, key_bytes, false, mem_budget,
+                     static_cast<cudaStream_t>(stream));
+}
+
+ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t count,
+                                     uint64_t mem_budget, ley_stream_t stream) {
+    if (count == 0) return LEY_OK;
+    if (!reqs) return LEY_EINVAL;
+    std::vector<BatchReq> v;
+    v.reserve(count);
+    ull npos = 0;
+    for (uint32_t r = 0; r < count; r++) {
+        const ley_pairs_request& q = reqs[r];
+        if (q.n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+        if (q.n == 0) continue;
+        if (!q.keys_in || !q.idx_in || !q.keys_out || !q.idx_out) return LEY_EINVAL;
+        const ull n = q.n;
+        if (overlaps(q.keys_in, n * 8, q.keys_out, n * 8) ||
+            overlaps(q.idx_in, n * 4, q.idx_out, n * 4) ||
+            overlaps(q.keys_in, n * 8, q.idx_out, n * 4) ||
+            overlaps(q.idx_in, n * 4, q.keys_out, n * 8))
+            return LEY_EINVAL;
+        if (((uintptr_t)q.keys_in & 7u) || ((uintptr_t)q.keys_out & 7u) ||
+            ((uintptr_t)q.idx_in & 3u) || ((uintptr_t)q.idx_out & 3u))
+            return LEY_EINVAL;
+        if (mem_kind(q.keys_in) != MK_DEVICE || mem_kind(q.idx_in) != MK_DEVICE ||
+            mem_kind(q.keys_out) != MK_DEVICE || mem_kind(q.idx_out) != MK_DEVICE)
+            return LEY_EINVAL;
+        BatchReq b{};
+        b.in = reinterpret_cast<const uint8_t*>(q.keys_in);
+        b.out = reinterpret_cast<uint8_t*>(q.keys_out);
+        b.idx_in = q.idx_in;
+        b.idx_out = q.idx_out;
+        b.n = n;
+        b.off = npos;
+        npos += (ull)ceil_div_u64(n, kPassTile) * kPassTile;
+        v.push_back(b);
+    }
+    if (v.empty()) return LEY_OK;
+    if (npos >= (1ull << 32)) return LEY_EUNSUPPORTED;
+    return run_batch(v, npos, 8, 8, true, mem_budget, static_cast<cudaStream_t>(stream));
 }
 
 ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,

@@ -154,6 +154,18 @@ struct Work {
 #define LEY_PHASE(k)
 #endif
 
+// One request of a batched sort.  Requests lie back to back in the batch's
+// tuple space, each starting on a tile boundary: request r owns tuple
+// positions [off, off + n), and its tuples carry indices local to it.
+struct BatchReq {
+    const uint8_t* in;       // records, or u64 keys
+    uint8_t* out;            // records, or u64 keys
+    const uint32_t* idx_in;  // pairs: payloads
+    uint32_t* idx_out;
+    unsigned long long n;
+    unsigned long long off;  // multiple of kPassTile
+};
+
 __host__ __device__ inline uint32_t ceil_div_u64(unsigned long long a, unsigned long long b) {
     return (uint32_t)((a + b - 1) / b);
 }

@@ -64,6 +64,24 @@ cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
 cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
                               const uint32_t* perm, unsigned long long n, unsigned long long n_in,
                               uint32_t rec_bytes, int variant, uint32_t* err);
+// Batched sorts (requests back to back in one tuple space, see BatchReq).
+cudaError_t launch_batch_setup(cudaStream_t s, const BatchReq* reqs, uint32_t R, const Work& w,
+                               uint32_t* tile_req, uint32_t ntiles, int digit0);
+cudaError_t launch_batch_extract_records(const LaunchCfg& c, const BatchReq* reqs,
+                                         const uint32_t* tile_req, uint32_t ntiles, uint32_t rec,
+                                         KeySpec ks, const Work& w);
+cudaError_t launch_batch_extract_pairs(const LaunchCfg& c, const BatchReq* reqs,
+                                       const uint32_t* tile_req, uint32_t ntiles, const Work& w);
+// Finish of a batch: 100-byte records gathered into place (pairs = false), or
+// sorted keys and payloads (pairs = true), into each request's own arrays.
+cudaError_t launch_batch_finish(const LaunchCfg& c, const Work& w, KeySpec ks,
+                                const BatchReq* reqs, const uint32_t* tile_req, bool pairs);
+cudaError_t launch_batch_gather_generic(cudaStream_t s, int grid, const BatchReq* reqs,
+                                        const uint32_t* tile_req, const uint32_t* perm,
+                                        unsigned long long npos, uint32_t rec, uint32_t* err);
+// dst[0, bytes) = src (host), stream-ordered through kernel parameters (no
+// host buffer needs to outlive the call; capturable in a CUDA graph).
+cudaError_t launch_upload(cudaStream_t s, void* dst, const void* src, size_t bytes);
 cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsigned long long n,
                                  uint32_t* order_out, unsigned long long* hist_out);
 

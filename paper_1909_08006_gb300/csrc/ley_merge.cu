@@ -12,6 +12,8 @@
 #define LEY_FILE_ID 3
 #include "ley_kernels.h"
 
+#include <cstring>
+
 namespace ley {
 
 using ull = unsigned long long;
@@ -140,6 +142,30 @@ cudaError_t launch_set_offsets(cudaStream_t s, ull* dst, const ull* host, uint32
     for (uint32_t i = 0; i < count; i++) b.v[i] = host[i];
     k_set_offsets<<<1, 128, 0, s>>>(dst, b, count);
     return cudaGetLastError();
+}
+
+// Host bytes to device memory through kernel parameters, 4 KB per launch.
+constexpr int kUploadChunk = 4000;
+struct UploadBlock {
+    unsigned char b[kUploadChunk];
+};
+
+__global__ void k_upload(unsigned char* dst, UploadBlock blk, uint32_t bytes) {
+    for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = blk.b[i];
+}
+
+cudaError_t launch_upload(cudaStream_t s, void* dst, const void* src, size_t bytes) {
+    const unsigned char* h = static_cast<const unsigned char*>(src);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    for (size_t o = 0; o < bytes; o += kUploadChunk) {
+        const uint32_t m = (uint32_t)(bytes - o < (size_t)kUploadChunk ? bytes - o : kUploadChunk);
+        UploadBlock blk;
+        std::memcpy(blk.b, h + o, m);
+        k_upload<<<1, 256, 0, s>>>(d + o, blk, m);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Copies the tuples' input positions (the w field) out as the permutation.

@@ -285,6 +285,181 @@ k_extract_pairs(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ 
     if (threadIdx.x == 0) flush_diff(sh_d, w.diff[0]);
 }
 
+// ------------------------------------------------------------ batches
+//
+// A batch of R requests is one sort over R top-level segments: request r's
+// tuples occupy [off_r, off_r + n_r) (off_r on a tile boundary), and the
+// levels, the classification and the finish treat the requests as the
+// buckets of a level -- an MSD pass never moves a tuple out of its bucket,
+// so each request is sorted on its own, exactly as a single sort would.
+
+// Level-0 segment list: one segment per request, its tiles, its zeroed
+// key-difference mask.
+__global__ void k_batch_setup(const BatchReq* __restrict__ reqs, uint32_t R, Work w,
+                              uint32_t ntiles, int digit0) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        const BatchReq q = reqs[r];
+        Seg s;
+        s.start = q.off;
+        s.count = (uint32_t)q.n;
+        s.digit = (uint16_t)digit0;
+        s.buf = 0;
+        s.pad = 0;
+        w.segs[0][r] = s;
+        w.seg_tile_base[0][r] = (uint32_t)(q.off / kPassTile);
+        Diff z;
+        z.hi = 0;
+        z.lo = 0;
+        z.pad = 0;
+        w.diff[0][r] = z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        w.ctl->lvl[0].big_packed = ((ull)R << kPackShift) | ntiles;
+}
+
+// tile -> request (the last request starting at or before the tile), also
+// the level-0 tile owners.
+__global__ void k_batch_tiles(const BatchReq* __restrict__ reqs, uint32_t R, Work w,
+                              uint32_t* __restrict__ tile_req, uint32_t ntiles) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+         t += gridDim.x * blockDim.x) {
+        const ull pos = (ull)t * kPassTile;
+        uint32_t lo = 0, hi = R;  // first request with off > pos
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (reqs[mid].off <= pos) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t r = lo > 0 ? lo - 1 : 0;
+        tile_req[t] = r;
+        w.seg_tile_owner[0][t] = r;
+    }
+}
+
+// Batch extract: tile t belongs to request tile_req[t]; its tuples carry
+// indices local to the request; per-tile digit-0 counts as for one sort,
+// and the difference mask against the request's first key goes to its
+// segment.
+template <int REC>
+__global__ void __launch_bounds__(256)
+k_batch_extract_records(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ tile_req,
+                        uint32_t ntiles, uint32_t rec_rt, KeySpec ks, Work w, int hist_digit) {
+    __shared__ uint32_t sh_hist[kRadix];
+    __shared__ uint32_t sh_d[3];
+    const uint32_t kb = (uint32_t)ks.ndig;
+    uint4* __restrict__ tup = w.tup[0];
+    constexpr int U = 4;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t r = tile_req[t];
+        const BatchReq q = reqs[r];
+        const uint8_t* in = q.in;
+        const uint4 ref = load_record_key<REC>(in, 0, rec_rt, kb, ks);
+        __syncthreads();
+        sh_hist[threadIdx.x] = 0;
+        if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
+        __syncthreads();
+        const ull lbase = (ull)t * kPassTile - q.off;  // first local index of the tile
+        ull dhi = 0;
+        uint32_t dlo = 0;
+#pragma unroll 1
+        for (int k0 = 0; k0 < kPassTile / 256; k0 += U) {
+            uint4 tv[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = lbase + (k0 + u) * 256 + threadIdx.x;
+                tv[u] = i < q.n ? load_record_key<REC>(in, i, rec_rt, kb, ks) : ref;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = lbase + (k0 + u) * 256 + threadIdx.x;
+                uint32_t dg = 256u;
+                if (i < q.n) {
+                    tv[u].w = (uint32_t)i;
+                    tup[q.off + i] = tv[u];
+                    dg = digit_of(tv[u], hist_digit);
+                    dhi |= key_hi(tv[u]) ^ key_hi(ref);
+                    dlo |= tv[u].z ^ ref.z;
+                }
+                hist_add_vote(sh_hist, dg);
+            }
+        }
+        warp_or_diff(dhi, dlo, sh_d);
+        __syncthreads();
+        w.tile_cnt[(ull)t * kRadix + threadIdx.x] = sh_hist[threadIdx.x];
+        if (threadIdx.x == 0) flush_diff(sh_d, &w.diff[0][r]);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_batch_extract_pairs(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ tile_req,
+                      uint32_t ntiles, Work w) {
+    __shared__ uint32_t sh_hist[kRadix];
+    __shared__ uint32_t sh_d[3];
+    uint4* __restrict__ tup = w.tup[0];
+    constexpr int U = 8;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t r = tile_req[t];
+        const BatchReq q = reqs[r];
+        const uint64_t* keys = reinterpret_cast<const uint64_t*>(q.in);
+        const ull ref = __ldg(keys);
+        __syncthreads();
+        sh_hist[threadIdx.x] = 0;
+        if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
+        __syncthreads();
+        const ull lbase = (ull)t * kPassTile - q.off;
+        ull dhi = 0;
+#pragma unroll 1
+        for (int k0 = 0; k0 < kPassTile / 256; k0 += U) {
+            ull kk[U];
+            uint32_t vv[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = lbase + (k0 + u) * 256 + threadIdx.x;
+                kk[u] = i < q.n ? __ldg(keys + i) : ref;
+                vv[u] = i < q.n ? __ldg(q.idx_in + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const ull i = lbase + (k0 + u) * 256 + threadIdx.x;
+                uint32_t dg = 256u;
+                if (i < q.n) {
+                    tup[q.off + i] =
+                        make_uint4((uint32_t)kk[u], (uint32_t)(kk[u] >> 32), vv[u], (uint32_t)i);
+                    dg = (uint32_t)(kk[u] >> 56);
+                    dhi |= kk[u] ^ ref;
+                }
+                hist_add_vote(sh_hist, dg);
+            }
+        }
+        warp_or_diff(dhi, 0u, sh_d);
+        __syncthreads();
+        w.tile_cnt[(ull)t * kRadix + threadIdx.x] = sh_hist[threadIdx.x];
+        if (threadIdx.x == 0) flush_diff(sh_d, &w.diff[0][r]);
+    }
+}
+
+// Records of any size: out_r[j] = in_r[perm[off_r + j]], one warp per record.
+__global__ void __launch_bounds__(256)
+k_batch_gather_generic(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ tile_req,
+                       const uint32_t* __restrict__ perm, ull npos, uint32_t rec, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const ull warps = (ull)gridDim.x * (blockDim.x >> 5);
+    const uint32_t words = rec / 4;
+    for (ull pos = (ull)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pos < npos;
+         pos += warps) {
+        const BatchReq q = reqs[tile_req[pos / kPassTile]];
+        if (pos - q.off >= q.n) continue;  // padding after the request's last tuple
+        uint32_t pj = perm[pos];
+        if (pj >= q.n) {  // never for a valid permutation; keeps reads in bounds
+            if (lane == 0) LEY_FAIL(err, kErrCapacity);
+            pj = 0;
+        }
+        const uint32_t* sp = reinterpret_cast<const uint32_t*>(q.in + (ull)pj * rec);
+        uint32_t* dp = reinterpret_cast<uint32_t*>(q.out + (pos - q.off) * rec);
+        for (uint32_t k = lane; k < words; k += 32) dp[k] = __ldg(sp + k);
+    }
+}
+
 __global__ void k_init(Work w, ull n, int digit0) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         w.ctl->lvl[0].big_packed = (1ull << kPackShift) | ceil_div_u64(n, kPassTile);
@@ -884,6 +1059,54 @@ struct Emitter<2> {  // 100-byte records gathered straight into place
     ull n_in;        // records at `in`: every source index is below it
 };
 
+// Batched sorts: the task's request is found from its first position
+// (tile -> request table), and the task is emitted like a single sort whose
+// output arrays are shifted by the request's offset, so that global
+// positions index them directly (off is a multiple of kPassTile, so the
+// shifted record base keeps the output's 16-byte phase).
+template <>
+struct Emitter<3> {  // batch of 100-byte records, gathered straight into place
+    const BatchReq* reqs;
+    const uint32_t* tile_req;
+};
+template <>
+struct Emitter<4> {  // batch of pairs
+    const BatchReq* reqs;
+    const uint32_t* tile_req;
+};
+
+template <int MODE>
+struct TaskEmit {
+    using type = Emitter<MODE>;
+    static constexpr int mode = MODE;
+    __device__ static type get(const Emitter<MODE>& e, ull) { return e; }
+};
+template <>
+struct TaskEmit<3> {
+    using type = Emitter<2>;
+    static constexpr int mode = 2;
+    __device__ static type get(const Emitter<3>& e, ull start) {
+        const BatchReq q = e.reqs[e.tile_req[start / kPassTile]];
+        Emitter<2> t;
+        t.in = q.in;
+        t.out = q.out - q.off * 100ull;
+        t.n_in = q.n;
+        return t;
+    }
+};
+template <>
+struct TaskEmit<4> {
+    using type = Emitter<1>;
+    static constexpr int mode = 1;
+    __device__ static type get(const Emitter<4>& e, ull start) {
+        const BatchReq q = e.reqs[e.tile_req[start / kPassTile]];
+        Emitter<1> t;
+        t.keys = reinterpret_cast<uint64_t*>(q.out) - q.off;
+        t.idx = q.idx_out - q.off;
+        return t;
+    }
+};
+
 // Shared state of one finishing CTA.  B holds the task's tuples; order[j] is
 // the position in B of the tuple whose final place in the task is j.
 struct FinShared {
@@ -1309,12 +1532,13 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     pdl_enter();
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
-    __shared__ __align__(8) uint64_t gbar;  // MODE 2: the record windows' bulk copies
+    constexpr int TM = TaskEmit<MODE>::mode;  // how a task is emitted
+    __shared__ __align__(8) uint64_t gbar;  // TM 2: the record windows' bulk copies
     uint32_t gphase = 0;
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
     if (tid == 0) {
         S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
-        if (MODE == 2) {
+        if (TM == 2) {
             mbar_init(&gbar, 1);
             mbar_fence_init();
         }
@@ -1341,13 +1565,14 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             skip = true;
         }
         const uint4* src = w.tup[tk.buf & 1] + tk.start;
+        const typename TaskEmit<MODE>::type te = TaskEmit<MODE>::get(emit, tk.start);
         if (!skip && (tk.flags & 1)) {  // all keys equal: input order
-            if constexpr (MODE == 2) {
+            if constexpr (TM == 2) {
                 if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), nullptr, src, true,
-                                        tk.start, tk.count, emit, &gbar, gphase, w.err))
+                                        tk.start, tk.count, te, &gbar, gphase, w.err))
                     break;
             } else {
-                for (uint32_t i = tid; i < tk.count; i += kFinThreads) emit(tk.start + i, src[i]);
+                for (uint32_t i = tid; i < tk.count; i += kFinThreads) te(tk.start + i, src[i]);
             }
             skip = true;
         }
@@ -1377,7 +1602,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                 __syncthreads();
             }
             LEY_PHASE(13);
-            if constexpr (MODE == 2) {
+            if constexpr (TM == 2) {
                 // The task's source indices in final order (count <= kSmall
                 // entries over the counters, which are free now), then the
                 // records themselves.
@@ -1391,7 +1616,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                     sidx[j] = B[o].w;
                 }
                 if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), sidx, src, false,
-                                        tk.start, tk.count, emit, &gbar, gphase, w.err))
+                                        tk.start, tk.count, te, &gbar, gphase, w.err))
                     break;
             } else {
                 // Coalesced write of the task's final order.
@@ -1401,7 +1626,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                         LEY_FAIL(w.err, kErrCapacity);
                         o = 0;
                     }
-                    emit(tk.start + j, B[o]);
+                    te(tk.start + j, B[o]);
                 }
             }
             LEY_PHASE(14);
@@ -1431,6 +1656,53 @@ extern "C" int ley_phase_read(unsigned long long* out) {
 }
 namespace ley {
 #endif
+
+cudaError_t launch_batch_setup(cudaStream_t s, const BatchReq* reqs, uint32_t R, const Work& w,
+                               uint32_t* tile_req, uint32_t ntiles, int digit0) {
+    k_batch_setup<<<(R + 255) / 256, 256, 0, s>>>(reqs, R, w, ntiles, digit0);
+    if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+    k_batch_tiles<<<(ntiles + 255) / 256, 256, 0, s>>>(reqs, R, w, tile_req, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_extract_records(const LaunchCfg& c, const BatchReq* reqs,
+                                         const uint32_t* tile_req, uint32_t ntiles, uint32_t rec,
+                                         KeySpec ks, const Work& w) {
+    const int grid = (int)min((uint32_t)c.grid, ntiles);
+    if (rec == 100)
+        k_batch_extract_records<100><<<grid, 256, 0, c.stream>>>(reqs, tile_req, ntiles, rec, ks, w, 0);
+    else
+        k_batch_extract_records<0><<<grid, 256, 0, c.stream>>>(reqs, tile_req, ntiles, rec, ks, w, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_extract_pairs(const LaunchCfg& c, const BatchReq* reqs,
+                                       const uint32_t* tile_req, uint32_t ntiles, const Work& w) {
+    const int grid = (int)min((uint32_t)c.grid, ntiles);
+    k_batch_extract_pairs<<<grid, 256, 0, c.stream>>>(reqs, tile_req, ntiles, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finish(const LaunchCfg& c, const Work& w, KeySpec ks,
+                                const BatchReq* reqs, const uint32_t* tile_req, bool pairs) {
+    if (pairs) {
+        Emitter<4> e;
+        e.reqs = reqs;
+        e.tile_req = tile_req;
+        return launch_pdl(k_finish<4>, c.grid, kFinThreads, c.smem, c.stream, w, ks, e);
+    }
+    Emitter<3> e;
+    e.reqs = reqs;
+    e.tile_req = tile_req;
+    return launch_pdl(k_finish<3>, c.grid, kFinThreads, c.smem, c.stream, w, ks, e);
+}
+
+cudaError_t launch_batch_gather_generic(cudaStream_t s, int grid, const BatchReq* reqs,
+                                        const uint32_t* tile_req, const uint32_t* perm, ull npos,
+                                        uint32_t rec, uint32_t* err) {
+    k_batch_gather_generic<<<grid, 256, 0, s>>>(reqs, tile_req, perm, npos, rec, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, ull n, uint32_t rec,
                                    KeySpec ks, const Work& w, int hist_digit) {
@@ -1551,6 +1823,10 @@ int blocks_per_sm(KernelKind k) {
                              (int)kernel_smem(KK_FINISH_PAIRS));
         cudaFuncSetAttribute(k_finish<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kernel_smem(KK_FINISH_GATHER));
+        cudaFuncSetAttribute(k_finish<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kernel_smem(KK_FINISH_GATHER));
+        cudaFuncSetAttribute(k_finish<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kernel_smem(KK_FINISH_PAIRS));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_extract_records<100>, 256, 0);
         g_bps[KK_EXTRACT_REC] = v > 0 ? v : 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_extract_pairs, 256, 0);
