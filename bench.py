@@ -191,6 +191,8 @@ def run_ours(args, world, rank, local, pg):
         return run_pairs(args, world, rank, dev, stream, pg)
     if wl in ("partial", "external"):
         return run_host_mode(args, world, rank, dev, stream, pg)
+    if wl == "batch":
+        return run_batch(args, world, rank, dev, stream, pg)
     gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
     d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
     d_out = torch.empty_like(d_in)
@@ -338,6 +340,68 @@ def run_pairs(args, world, rank, dev, stream, pg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "gpu_launches": launches,
         "config": {"workload": f"pairs_{n}", "pairs": n, "bytes_per_pair": 12},
+    }
+
+
+def run_batch(args, world, rank, dev, stream, pg):
+    """Many sort requests of uneven sizes (log-uniform in [lo, hi] records),
+    half 100-byte records and half (u64 key, u32 payload) pairs: one batched
+    call per kind against one call per request, same stream, same data."""
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    count, lo, hi = args.requests, args.req_min, args.req_max
+    sizes = datagen.log_uniform_sizes(count, seed=5, lo=lo, hi=hi)
+    rec_reqs, pair_reqs = [], []
+    for i, n in enumerate(sizes):
+        if i % 2 == 0:
+            x = datagen.uniform_records(n, seed=1000 + i, device=dev)
+            rec_reqs.append((x, torch.empty_like(x)))
+        else:
+            k, v = datagen.uniform_pairs(n, seed=1000 + i, device=dev)
+            pair_reqs.append((k, v, torch.empty_like(k), torch.empty_like(v)))
+    n_rec = sum(int(r[0].shape[0]) for r in rec_reqs)
+    n_pair = sum(int(r[0].shape[0]) for r in pair_reqs)
+    total_bytes = n_rec * REC + n_pair * 12
+    torch.cuda.synchronize()
+
+    def batched():
+        ley.ley_sort_records_batch(rec_reqs, stream=stream)
+        ley.ley_sort_keys_index_batch(pair_reqs, stream=stream)
+
+    def one_by_one():
+        for x, o in rec_reqs:
+            ley.ley_sort_records(x, o, stream=stream)
+        for k, v, ko, vo in pair_reqs:
+            ley.ley_sort_keys_index(k, v, ko, vo, stream=stream)
+
+    launches0 = ley.ley_launch_count()
+    ms_b = _timed(batched, args.steps, args.warmup, stream, pg, dev)
+    launches_b = (ley.ley_launch_count() - launches0) // (args.steps + args.warmup)
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error")
+    outs_b = [o.clone() for _, o in rec_reqs] + [ko.clone() for _, _, ko, _ in pair_reqs]
+    launches0 = ley.ley_launch_count()
+    ms_s = _timed(one_by_one, args.steps, args.warmup, stream, pg, dev)
+    launches_s = (ley.ley_launch_count() - launches0) // (args.steps + args.warmup)
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error")
+    outs_s = [o for _, o in rec_reqs] + [ko for _, _, ko, _ in pair_reqs]
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
+    return {
+        "metric": "GB/s of request data sorted, batched (records + pairs)",
+        "value": round(world * total_bytes / (ms_b * 1e-3) / 1e9, 2), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_b, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic", "gpu_launches": launches_b,
+        "config": {"workload": f"batch_{count}x[{lo},{hi}]", "requests": count,
+                   "records": n_rec, "pairs": n_pair, "bytes": total_bytes,
+                   "sizes": "log-uniform, half 100-byte records, half (u64, u32) pairs"},
+        "one_launch_per_request": {
+            "value": round(world * total_bytes / (ms_s * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms_s, 3), "gpu_launches": launches_s},
+        "speedup_vs_one_launch_per_request": round(ms_s / ms_b, 3),
+        "identical_outputs": same,
     }
 
 
@@ -521,7 +585,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "skew", "pairs", "partial", "external"])
+                    choices=["uniform", "skew", "pairs", "partial", "external", "batch"])
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--req-min", type=int, default=1000)
+    ap.add_argument("--req-max", type=int, default=10_000_000)
     ap.add_argument("--budget-gb", type=float, default=30.0)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     args = ap.parse_args()
