@@ -193,6 +193,8 @@ def run_ours(args, world, rank, local, pg):
         return run_host_mode(args, world, rank, dev, stream, pg)
     if wl == "batch":
         return run_batch(args, world, rank, dev, stream, pg)
+    if wl == "serve":
+        return run_serve(args, world, rank, dev, stream, pg)
     gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
     d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
     d_out = torch.empty_like(d_in)
@@ -405,6 +407,131 @@ def run_batch(args, world, rank, dev, stream, pg):
     }
 
 
+def run_serve(args, world, rank, dev, stream, pg):
+    """Served sorting: a stream of requests (sizes log-uniform in [lo, hi],
+    half 100-byte records, half (u64, u32) pairs) through the continuous-
+    batching server under a device budget.  Saturation (all requests at t0)
+    gives the capacity, batched and with one request per launch; Poisson
+    arrivals at 0.5x and 0.9x of the batched capacity give p50/p99 latency.
+    Inputs are resident in HBM: P distinct inputs per kind drawn from the size
+    distribution, each with Q output buffers that requests rotate through."""
+    import threading
+    import numpy as np
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    count, lo, hi = args.requests, args.req_min, args.req_max
+    P, Q = args.serve_inputs, 4
+    budget = int(args.budget_gb * 1e9)
+    sizes = datagen.log_uniform_sizes(2 * P, seed=11, lo=lo, hi=hi)
+    ins, outs, alone, nbytes = [[], []], [[], []], [[], []], [[], []]
+    for b in range(P):
+        n = sizes[2 * b]
+        x = datagen.uniform_records(n, seed=3000 + b, device=dev)
+        ins[0].append(x)
+        outs[0].append([torch.empty_like(x) for _ in range(Q)])
+        a = torch.empty_like(x)
+        ley.ley_sort_records(x, a)
+        alone[0].append(a)
+        nbytes[0].append(n * REC)
+        n = sizes[2 * b + 1]
+        k, v = datagen.uniform_pairs(n, seed=4000 + b, device=dev)
+        ins[1].append((k, v))
+        outs[1].append([(torch.empty_like(k), torch.empty_like(v)) for _ in range(Q)])
+        ak, av = torch.empty_like(k), torch.empty_like(v)
+        ley.ley_sort_keys_index(k, v, ak, av)
+        alone[1].append((ak, av))
+        nbytes[1].append(n * 12)
+    torch.cuda.synchronize()
+
+    def plan(i):  # kind, input, output slot of request i
+        kind = i % 2
+        b = (i // 2) % P
+        return kind, b, (i // (2 * P)) % Q
+
+    def serve(max_batch, arrivals):
+        srv = ley.ley_server_create(budget, max_batch=max_batch, slots=args.serve_slots)
+        free = {}
+        lat, done_t, bad = [None] * count, [0.0] * count, [0]
+        tickets = [None] * count
+        ready = [threading.Event() for _ in range(count)]
+        base = time.perf_counter()
+
+        def waiter():
+            for i in range(count):
+                ready[i].wait()
+                tm = ley.ley_server_wait(srv, tickets[i][0])
+                late = tickets[i][1]  # submission lateness against the scheduled arrival
+                lat[i] = tm["done_s"] - tm["submit_s"] + late
+                done_t[i] = tm["done_s"]
+                kind, b, q = plan(i)
+                if i % 32 == 0:
+                    o = outs[kind][b][q]
+                    same = torch.equal(o, alone[0][b]) if kind == 0 else (
+                        torch.equal(o[0], alone[1][b][0]) and torch.equal(o[1], alone[1][b][1]))
+                    bad[0] += 0 if same else 1
+                free[(kind, b, q)].set()
+
+        w = threading.Thread(target=waiter)
+        w.start()
+        t_first = None
+        for i in range(count):
+            kind, b, q = plan(i)
+            ev = free.get((kind, b, q))
+            if ev is not None:
+                ev.wait()  # the output slot's previous request is done
+            free[(kind, b, q)] = threading.Event()
+            target = base + arrivals[i]
+            now = time.perf_counter()
+            if target > now:
+                time.sleep(target - now)
+            late = max(0.0, time.perf_counter() - target)
+            if kind == 0:
+                t = ley.ley_server_submit_records(srv, ins[0][b], outs[0][b][q])
+            else:
+                (k, v), (ko, vo) = ins[1][b], outs[1][b][q]
+                t = ley.ley_server_submit_pairs(srv, k, v, ko, vo)
+            if t_first is None:
+                t_first = time.perf_counter()
+            tickets[i] = (t, late)
+            ready[i].set()
+        w.join()
+        st = ley.ley_server_stats(srv)
+        ley.ley_server_destroy(srv)
+        total = sum(nbytes[plan(i)[0]][plan(i)[1]] for i in range(count))
+        arr = np.array(lat)
+        makespan = max(done_t)  # seconds since the server's creation (just before base)
+        return {"GBps": round(total / makespan / 1e9, 2), "makespan_s": round(makespan, 4),
+                "req_per_s": round(count / makespan, 1),
+                "p50_ms": round(float(np.percentile(arr, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(arr, 99)) * 1e3, 3),
+                "batches": st["launched_batches"], "checked": count // 32 + (count % 32 > 0),
+                "mismatches": bad[0], "bytes": total}
+
+    zero = [0.0] * count
+    sat = serve(args.serve_batch, zero)
+    single = serve(1, zero)
+    rng = np.random.default_rng(12)
+    res = {}
+    for frac in (0.5, 0.9):
+        rate = frac * sat["req_per_s"]
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count)).tolist()
+        res[f"poisson_{frac}"] = serve(args.serve_batch, arrivals)
+        res[f"poisson_{frac}"]["rate_req_per_s"] = round(rate, 1)
+    return {
+        "metric": "GB/s of request data sorted by the batching server (saturation); p50/p99",
+        "value": sat["GBps"], "unit": "GB/s", "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": round(sat["makespan_s"] * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"serve_{count}x[{lo},{hi}]", "requests": count,
+                   "budget_bytes": budget, "max_batch": args.serve_batch,
+                   "slots": args.serve_slots, "distinct_inputs_per_kind": P},
+        "saturation": sat, "one_launch_per_request": single,
+        "speedup_vs_one_launch_per_request": round(single["makespan_s"] / sat["makespan_s"], 3),
+        **res,
+    }
+
+
 def _libcuda():
     import ctypes
     cu = ctypes.CDLL("libcuda.so.1")
@@ -585,8 +712,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "skew", "pairs", "partial", "external", "batch"])
-    ap.add_argument("--requests", type=int, default=256)
+                    choices=["uniform", "skew", "pairs", "partial", "external", "batch",
+                             "serve"])
+    ap.add_argument("--serve-batch", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-inputs", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=None)
     ap.add_argument("--req-min", type=int, default=1000)
     ap.add_argument("--req-max", type=int, default=10_000_000)
     ap.add_argument("--budget-gb", type=float, default=30.0)
@@ -597,6 +728,10 @@ def main():
         args.n = 400_000_000
     if args.workload == "partial" and args.n == 100_000_000:
         args.n = 200_000_000
+    if args.workload == "serve" and args.budget_gb == 30.0:
+        args.budget_gb = 40.0
+    if args.requests is None:
+        args.requests = 10_000 if args.workload == "serve" else 256
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         out = run_reference(args, world, rank, pg)

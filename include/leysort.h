@@ -129,6 +129,56 @@ ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t cou
                                      uint64_t mem_budget, ley_stream_t stream);
 
 /*
+ * Sort server: continuous batching of sort requests on the current device.
+ * The paper has no counterpart (it sorts one data set per run); this is the
+ * serving form of the batched sorts above.
+ *
+ * Requests are submitted from any host thread with their device buffers
+ * already allocated (same rules as the single-request calls); submission
+ * never blocks on the GPU.  A scheduler thread admits pending requests in
+ * arrival order into a batch while one of `slots` launch streams is free and
+ * the request's device memory -- its input and output plus its share of the
+ * sort scratch -- fits `mem_budget` together with everything already in
+ * flight (a single request larger than the budget runs alone).  Requests that
+ * arrive while batches run join the next batch as soon as a slot and memory
+ * free up, so batches on different slots overlap on the device.  At most
+ * `max_batch` requests go into one batch.  Every request is sorted exactly as
+ * its own ley_sort_records / ley_sort_keys_index call would sort it.
+ *
+ * Submission checks the request's arguments like the single-request call
+ * (a rejected request gets no ticket).  ley_server_wait blocks until the request is done, returns its status (as
+ * ley_last_device_status would report it for the batch that carried it) and
+ * its submit / launch / completion times in seconds since the server was
+ * created; a ticket can be waited for once.  ley_server_destroy finishes all
+ * submitted work, then stops the server's threads.
+ */
+typedef struct ley_server ley_server;
+
+typedef struct {
+    double submit_s;  /* submission */
+    double start_s;   /* its batch was launched */
+    double done_s;    /* its batch's completion was observed on the host */
+} ley_server_times;
+
+typedef struct {
+    uint64_t pending;           /* submitted, not yet admitted */
+    uint64_t inflight_batches;  /* launched, not yet completed */
+    uint64_t launched_batches;  /* since creation */
+    uint64_t bytes_in_use;      /* device bytes charged to admitted requests */
+} ley_server_counters;
+
+ley_status ley_server_create(ley_server** server, uint64_t mem_budget, uint32_t max_batch,
+                             uint32_t slots);
+ley_status ley_server_submit_records(ley_server* server, const void* in, void* out, uint64_t n,
+                                     uint32_t rec_bytes, uint32_t key_bytes, uint64_t* ticket);
+ley_status ley_server_submit_pairs(ley_server* server, const uint64_t* keys_in,
+                                   const uint32_t* idx_in, uint64_t* keys_out, uint32_t* idx_out,
+                                   uint64_t n, uint64_t* ticket);
+ley_status ley_server_wait(ley_server* server, uint64_t ticket, ley_server_times* times);
+ley_status ley_server_stats(ley_server* server, ley_server_counters* counters);
+ley_status ley_server_destroy(ley_server* server);
+
+/*
  * One round of Algorithm 1 (Section 3.1, "Cache Aware Scattering Process"):
  * the histogram of key byte `digit` and the stable partition of the records
  * into the 256 buckets of that byte.

@@ -24,6 +24,8 @@ __all__ = [
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
     "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS", "ley_merge_records",
     "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
+    "ley_server_create", "ley_server_submit_records", "ley_server_submit_pairs",
+    "ley_server_wait", "ley_server_stats", "ley_server_destroy",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -49,6 +51,16 @@ class _PairsReq(ctypes.Structure):
     _fields_ = [("keys_in", ctypes.c_void_p), ("idx_in", ctypes.c_void_p),
                 ("keys_out", ctypes.c_void_p), ("idx_out", ctypes.c_void_p),
                 ("n", ctypes.c_uint64)]
+
+
+class _ServerTimes(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class _ServerCounters(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_uint64), ("inflight_batches", ctypes.c_uint64),
+                ("launched_batches", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -94,6 +106,18 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_records_batch.restype = ctypes.c_int
     lib.ley_sort_keys_index_batch.argtypes = [ctypes.POINTER(_PairsReq), u32, u64, vp]
     lib.ley_sort_keys_index_batch.restype = ctypes.c_int
+    lib.ley_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
+    lib.ley_server_create.restype = ctypes.c_int
+    lib.ley_server_submit_records.argtypes = [vp, vp, vp, u64, u32, u32, ctypes.POINTER(u64)]
+    lib.ley_server_submit_records.restype = ctypes.c_int
+    lib.ley_server_submit_pairs.argtypes = [vp, vp, vp, vp, vp, u64, ctypes.POINTER(u64)]
+    lib.ley_server_submit_pairs.restype = ctypes.c_int
+    lib.ley_server_wait.argtypes = [vp, u64, ctypes.POINTER(_ServerTimes)]
+    lib.ley_server_wait.restype = ctypes.c_int
+    lib.ley_server_stats.argtypes = [vp, ctypes.POINTER(_ServerCounters)]
+    lib.ley_server_stats.restype = ctypes.c_int
+    lib.ley_server_destroy.argtypes = [vp]
+    lib.ley_server_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -194,6 +218,57 @@ def ley_sort_keys_index_batch(requests, mem_budget: int = 0, stream=None) -> int
         st = _stream(stream)
     return _check(_lib.ley_sort_keys_index_batch(arr, len(requests), mem_budget, st),
                   "ley_sort_keys_index_batch")
+
+
+# ---------------------------------------------------------------- server
+
+def ley_server_create(mem_budget: int, max_batch: int = 256, slots: int = 3) -> int:
+    """A continuous-batching sort server on the current device (a handle)."""
+    h = ctypes.c_void_p()
+    _check(_lib.ley_server_create(ctypes.byref(h), int(mem_budget), max_batch, slots),
+           "ley_server_create")
+    return int(h.value)
+
+
+def ley_server_submit_records(server: int, inp, out, n: int | None = None,
+                              rec_bytes: int | None = None, key_bytes: int = 10) -> int:
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
+    t = ctypes.c_uint64(0)
+    _check(_lib.ley_server_submit_records(server, _addr(inp), _addr(out), n, rec_bytes,
+                                          key_bytes, ctypes.byref(t)), "ley_server_submit_records")
+    return int(t.value)
+
+
+def ley_server_submit_pairs(server: int, keys_in, idx_in, keys_out, idx_out,
+                            n: int | None = None) -> int:
+    if n is None:
+        n = int(keys_in.shape[0])
+    t = ctypes.c_uint64(0)
+    _check(_lib.ley_server_submit_pairs(server, _addr(keys_in), _addr(idx_in), _addr(keys_out),
+                                        _addr(idx_out), n, ctypes.byref(t)),
+           "ley_server_submit_pairs")
+    return int(t.value)
+
+
+def ley_server_wait(server: int, ticket: int) -> dict:
+    """Blocks until the request is done; raises LeyError on a failed request.
+    Returns its submit / start / done times (seconds since server creation)."""
+    tm = _ServerTimes()
+    _check(_lib.ley_server_wait(server, ticket, ctypes.byref(tm)), "ley_server_wait")
+    return {"submit_s": tm.submit_s, "start_s": tm.start_s, "done_s": tm.done_s}
+
+
+def ley_server_stats(server: int) -> dict:
+    c = _ServerCounters()
+    _check(_lib.ley_server_stats(server, ctypes.byref(c)), "ley_server_stats")
+    return {f: int(getattr(c, f)) for f, _ in _ServerCounters._fields_}
+
+
+def ley_server_destroy(server: int) -> int:
+    return _check(_lib.ley_server_destroy(server), "ley_server_destroy")
 
 
 def ley_sort_records_noalloc(inp, out, n: int | None = None, rec_bytes: int | None = None,

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libleysort.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["ley_radix.cu", "ley_gather.cu", "ley_merge.cu", "ley_api.cu"]
+SOURCES = ["ley_radix.cu", "ley_gather.cu", "ley_merge.cu", "ley_api.cu", "ley_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-v", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -987,6 +987,43 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace ley
 
+namespace ley {
+// Argument checks of one request of a batch (also used by the sort server
+// at submission).
+ley_status check_records_request(const ley_records_request& q, uint32_t rec_bytes,
+                                 uint32_t key_bytes) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u) || q.n >= (1ull << 32))
+        return LEY_EUNSUPPORTED;
+    if (q.n == 0) return LEY_OK;
+    if (!q.in || !q.out) return LEY_EINVAL;
+    const ull bytes = q.n * rec_bytes;
+    if (overlaps(q.in, bytes, q.out, bytes)) return LEY_EINVAL;
+    if (!aligned16(q.in) || !aligned16(q.out)) return LEY_EINVAL;
+    if (mem_kind(q.in) != MK_DEVICE || mem_kind(q.out) != MK_DEVICE) return LEY_EINVAL;
+    return LEY_OK;
+}
+
+ley_status check_pairs_request(const ley_pairs_request& q) {
+    if (q.n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+    if (q.n == 0) return LEY_OK;
+    if (!q.keys_in || !q.idx_in || !q.keys_out || !q.idx_out) return LEY_EINVAL;
+    const ull n = q.n;
+    if (overlaps(q.keys_in, n * 8, q.keys_out, n * 8) ||
+        overlaps(q.idx_in, n * 4, q.idx_out, n * 4) ||
+        overlaps(q.keys_in, n * 8, q.idx_out, n * 4) ||
+        overlaps(q.idx_in, n * 4, q.keys_out, n * 8))
+        return LEY_EINVAL;
+    if (((uintptr_t)q.keys_in & 7u) || ((uintptr_t)q.keys_out & 7u) ||
+        ((uintptr_t)q.idx_in & 3u) || ((uintptr_t)q.idx_out & 3u))
+        return LEY_EINVAL;
+    if (mem_kind(q.keys_in) != MK_DEVICE || mem_kind(q.idx_in) != MK_DEVICE ||
+        mem_kind(q.keys_out) != MK_DEVICE || mem_kind(q.idx_out) != MK_DEVICE)
+        return LEY_EINVAL;
+    return LEY_OK;
+}
+}  // namespace ley
+
 // ================================================================ C ABI
 
 using namespace ley;
@@ -1044,6 +1081,7 @@ ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
     return run_device_sort(a, mem_budget, static_cast<cudaStream_t>(stream));
 }
 
+
 ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t count,
                                   uint32_t rec_bytes, uint32_t key_bytes, uint64_t mem_budget,
                                   ley_stream_t stream) {
@@ -1057,13 +1095,9 @@ ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t coun
     ull npos = 0;
     for (uint32_t r = 0; r < count; r++) {
         const ley_records_request& q = reqs[r];
-        if (q.n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+        const ley_status c = check_records_request(q, rec_bytes, key_bytes);
+        if (c != LEY_OK) return c;
         if (q.n == 0) continue;
-        if (!q.in || !q.out) return LEY_EINVAL;
-        const ull bytes = q.n * rec_bytes;
-        if (overlaps(q.in, bytes, q.out, bytes)) return LEY_EINVAL;
-        if (!aligned16(q.in) || !aligned16(q.out)) return LEY_EINVAL;
-        if (mem_kind(q.in) != MK_DEVICE || mem_kind(q.out) != MK_DEVICE) return LEY_EINVAL;
         BatchReq b{};
         b.in = static_cast<const uint8_t*>(q.in);
         b.out = static_cast<uint8_t*>(q.out);
@@ -1087,21 +1121,10 @@ ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t cou
     ull npos = 0;
     for (uint32_t r = 0; r < count; r++) {
         const ley_pairs_request& q = reqs[r];
-        if (q.n >= (1ull << 32)) return LEY_EUNSUPPORTED;
+        const ley_status c = check_pairs_request(q);
+        if (c != LEY_OK) return c;
         if (q.n == 0) continue;
-        if (!q.keys_in || !q.idx_in || !q.keys_out || !q.idx_out) return LEY_EINVAL;
         const ull n = q.n;
-        if (overlaps(q.keys_in, n * 8, q.keys_out, n * 8) ||
-            overlaps(q.idx_in, n * 4, q.idx_out, n * 4) ||
-            overlaps(q.keys_in, n * 8, q.idx_out, n * 4) ||
-            overlaps(q.idx_in, n * 4, q.keys_out, n * 8))
-            return LEY_EINVAL;
-        if (((uintptr_t)q.keys_in & 7u) || ((uintptr_t)q.keys_out & 7u) ||
-            ((uintptr_t)q.idx_in & 3u) || ((uintptr_t)q.idx_out & 3u))
-            return LEY_EINVAL;
-        if (mem_kind(q.keys_in) != MK_DEVICE || mem_kind(q.idx_in) != MK_DEVICE ||
-            mem_kind(q.keys_out) != MK_DEVICE || mem_kind(q.idx_out) != MK_DEVICE)
-            return LEY_EINVAL;
         BatchReq b{};
         b.in = reinterpret_cast<const uint8_t*>(q.keys_in);
         b.out = reinterpret_cast<uint8_t*>(q.keys_out);
