@@ -187,6 +187,19 @@ def run_ours(args, world, rank, local, pg):
     n = args.n
     stream = torch.cuda.Stream(dev)
     wl = args.workload
+    tuning = None
+    if args.autotune:
+        tuning = ley.ley_autotune_records(min(n, 100_000_000), REC, KEY)
+    out = _run_workload(args, world, rank, local, pg, dev, stream, wl, n)
+    if out is not None:
+        out["tuning"] = tuning if tuning is not None else ley.ley_get_tuning()
+    return out
+
+
+def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
     if wl == "pairs":
         return run_pairs(args, world, rank, dev, stream, pg)
     if wl in ("partial", "external"):
@@ -714,6 +727,8 @@ def main():
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "skew", "pairs", "partial", "external", "batch",
                              "serve"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the library's autotuner on the workload's size first")
     ap.add_argument("--serve-batch", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-inputs", type=int, default=64)

@@ -224,6 +224,39 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
  */
 ley_status ley_release_cache(void);
 
+/*
+ * Tunables of the sort on the current device.  None of them changes a
+ * result; they decide which path a bucket takes (the bigBucketThreshold and
+ * tinyBucketThreshold of Section 3.1, Algorithm 1, which the paper leaves
+ * unstated) and how many CTAs per SM the finishing and scatter kernels run.
+ * They apply to sorts started after ley_set_tuning returns (set them when no
+ * other thread is starting sorts).  The allocation-free entry point always
+ * uses the defaults.
+ */
+typedef struct {
+    uint32_t big_bucket;          /* buckets above this many tuples are scattered again;
+                                     256..2048, default 2048 (one finishing CTA's capacity) */
+    uint32_t tiny_bucket;         /* sub-buckets up to this many tuples are finished by
+                                     comparison ranking; 32..256, default 32 */
+    uint32_t finish_ctas_per_sm;  /* 0 = as many as fit (default) */
+    uint32_t pass_ctas_per_sm;    /* 0 = as many as fit (default) */
+} ley_tuning;
+
+ley_status ley_get_tuning(ley_tuning* tuning);
+/* NULL restores the defaults; out-of-range values are LEY_EINVAL. */
+ley_status ley_set_tuning(const ley_tuning* tuning);
+
+/*
+ * Autotuner: sorts n uniform random records of this geometry (generated on
+ * the device from `seed`) under each of a grid of tunings -- big bucket
+ * 2048 / 1536 / 1024, tiny bucket 32 / 64 / 128, finishing CTAs per SM as
+ * many as fit / 3 -- keeps the fastest (best of two timed sorts each, after
+ * one warm-up), makes it the current tuning and returns it in *best.
+ * Allocates 2 * n * rec_bytes bytes plus one sort's scratch; blocks.
+ */
+ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                                uint64_t seed, ley_tuning* best);
+
 /* Static English text for a status code (never NULL). */
 const char* ley_status_string(ley_status s);
 

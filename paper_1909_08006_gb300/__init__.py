@@ -26,6 +26,7 @@ __all__ = [
     "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
     "ley_server_create", "ley_server_submit_records", "ley_server_submit_pairs",
     "ley_server_wait", "ley_server_stats", "ley_server_destroy",
+    "ley_get_tuning", "ley_set_tuning", "ley_autotune_records",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -51,6 +52,11 @@ class _PairsReq(ctypes.Structure):
     _fields_ = [("keys_in", ctypes.c_void_p), ("idx_in", ctypes.c_void_p),
                 ("keys_out", ctypes.c_void_p), ("idx_out", ctypes.c_void_p),
                 ("n", ctypes.c_uint64)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("big_bucket", ctypes.c_uint32), ("tiny_bucket", ctypes.c_uint32),
+                ("finish_ctas_per_sm", ctypes.c_uint32), ("pass_ctas_per_sm", ctypes.c_uint32)]
 
 
 class _ServerTimes(ctypes.Structure):
@@ -106,6 +112,12 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_records_batch.restype = ctypes.c_int
     lib.ley_sort_keys_index_batch.argtypes = [ctypes.POINTER(_PairsReq), u32, u64, vp]
     lib.ley_sort_keys_index_batch.restype = ctypes.c_int
+    lib.ley_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
+    lib.ley_get_tuning.restype = ctypes.c_int
+    lib.ley_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
+    lib.ley_set_tuning.restype = ctypes.c_int
+    lib.ley_autotune_records.argtypes = [u64, u32, u32, u64, ctypes.POINTER(_Tuning)]
+    lib.ley_autotune_records.restype = ctypes.c_int
     lib.ley_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
     lib.ley_server_create.restype = ctypes.c_int
     lib.ley_server_submit_records.argtypes = [vp, vp, vp, u64, u32, u32, ctypes.POINTER(u64)]
@@ -218,6 +230,34 @@ def ley_sort_keys_index_batch(requests, mem_budget: int = 0, stream=None) -> int
         st = _stream(stream)
     return _check(_lib.ley_sort_keys_index_batch(arr, len(requests), mem_budget, st),
                   "ley_sort_keys_index_batch")
+
+
+# ---------------------------------------------------------------- tuning
+
+def ley_get_tuning() -> dict:
+    t = _Tuning()
+    _check(_lib.ley_get_tuning(ctypes.byref(t)), "ley_get_tuning")
+    return {f: int(getattr(t, f)) for f, _ in _Tuning._fields_}
+
+
+def ley_set_tuning(tuning: dict | None) -> int:
+    """Set the current device's tunables (dict with the ley_tuning fields);
+    None restores the defaults."""
+    if tuning is None:
+        return _check(_lib.ley_set_tuning(None), "ley_set_tuning")
+    t = _Tuning(**{f: int(tuning.get(f, d)) for f, d in
+                   (("big_bucket", 2048), ("tiny_bucket", 32), ("finish_ctas_per_sm", 0),
+                    ("pass_ctas_per_sm", 0))})
+    return _check(_lib.ley_set_tuning(ctypes.byref(t)), "ley_set_tuning")
+
+
+def ley_autotune_records(n: int, rec_bytes: int = 100, key_bytes: int = 10,
+                         seed: int = 1) -> dict:
+    """Times a grid of tunings on n random records; keeps and returns the fastest."""
+    t = _Tuning()
+    _check(_lib.ley_autotune_records(n, rec_bytes, key_bytes, seed, ctypes.byref(t)),
+           "ley_autotune_records")
+    return {f: int(getattr(t, f)) for f, _ in _Tuning._fields_}
 
 
 # ---------------------------------------------------------------- server

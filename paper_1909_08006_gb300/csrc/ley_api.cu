@@ -31,6 +31,24 @@ struct DevState {
 };
 static DevState g_dev[64];
 static std::mutex g_mu;
+
+// Tunables of the sort (ley_set_tuning / ley_autotune_records), per device.
+// None of them changes a result: Algorithm 1's thresholds only decide which
+// bucket takes which path.
+struct Tuning {
+    uint32_t big = kSmall;   // big-bucket threshold (bigBucketThreshold)
+    uint32_t tiny = kTiny;   // tiny-bucket threshold (tinyBucketThreshold)
+    uint32_t fin_ctas = 0;   // finishing CTAs per SM, 0 = as many as fit
+    uint32_t pass_ctas = 0;  // scatter CTAs per SM, 0 = as many as fit
+};
+static Tuning g_tune[64];
+
+static Tuning cur_tuning() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return Tuning{};
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_tune[d];
+}
 static std::atomic<unsigned long long> g_launches{0};
 
 // The record path reads 10..12-byte keys out of 100-byte records (extract)
@@ -171,12 +189,12 @@ struct Layout {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static Layout make_layout(ull n, bool with_perm) {
+static Layout make_layout(ull n, bool with_perm, uint32_t big = cur_tuning().big) {
     Layout L{};
-    L.cap_seg = n / kSmall + 2;
+    L.cap_seg = n / big + 2;
     L.cap_tiles = n / kPassTile + L.cap_seg + 1;
     L.cap_chunks = L.cap_tiles / kScanChunk + 1;
-    L.cap_fin = 100 * (n / kSmall + 1) + 16;
+    L.cap_fin = 100 * (n / big + 1) + 16;
     size_t off = 0;
     auto put = [&](size_t bytes) {
         size_t o = off;
@@ -230,16 +248,20 @@ static Work make_work(char* base, const Layout& L, ull n, uint32_t* err) {
     return w;
 }
 
-static KeySpec record_keyspec(uint32_t kb) {
+static KeySpec record_keyspec(uint32_t kb, const Tuning& t = cur_tuning()) {
     KeySpec ks;
+    ks.big = t.big;
+    ks.tiny = t.tiny;
     ks.ndig = (int)kb;
     ks.hi_mask = kb >= 8 ? ~0ull : (~0ull << (64 - 8 * kb));
     ks.lo_mask = kb <= 8 ? 0u : (kb >= 12 ? ~0u : (~0u << (32 - 8 * (kb - 8))));
     return ks;
 }
 
-static KeySpec pair_keyspec() {
+static KeySpec pair_keyspec(const Tuning& t = cur_tuning()) {
     KeySpec ks;
+    ks.big = t.big;
+    ks.tiny = t.tiny;
     ks.ndig = 8;
     ks.hi_mask = ~0ull;
     ks.lo_mask = 0u;
@@ -308,8 +330,17 @@ static ley_status stage_extract_records(const SortArgs& a, const Work& w, const 
 
 // The MSD levels (histogram, offset scan, classify, scatter) and the
 // small-bucket finish; records mode leaves the permutation in w.perm.
+// Persistent grids: CTAs per SM as the tuning asks, at most what fits.
+static int tuned_grid(int sms, KernelKind k, uint32_t want) {
+    int b = blocks_per_sm(k);
+    if (want && (int)want < b) b = (int)want;
+    return sms * b;
+}
+static int pass_grid(int sms) { return tuned_grid(sms, KK_PASS, cur_tuning().pass_ctas); }
+static int fin_grid(int sms, KernelKind k) { return tuned_grid(sms, k, cur_tuning().fin_ctas); }
+
 static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st, int sms) {
-    const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
+    const LaunchCfg cp{pass_grid(sms), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
     const LaunchCfg cc{2 * sms, 128, 0, st};
@@ -327,7 +358,7 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
     ley_status s0 = stage_levels(w, ks, st, sms);
     if (s0 != LEY_OK) return s0;
     if (a.mode == MODE_PAIRS) {
-        LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_PAIRS), kFinThreads,
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_PAIRS), kFinThreads,
                      kernel_smem(KK_FINISH_PAIRS), st};
         LEY_TRY(launch("finish", st, [&] {
             return launch_finish_pairs(cf, w, ks, a.keys_out, a.idx_out);
@@ -335,14 +366,14 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
         return LEY_OK;
     }
     if (fuse) {  // records gathered into a.out by the finishing kernel itself
-        LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_GATHER), kFinThreads,
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_GATHER), kFinThreads,
                      kernel_smem(KK_FINISH_GATHER), st};
         LEY_TRY(launch("finish_gather", st, [&] {
             return launch_finish_gather(cf, w, ks, a.in, a.out, a.n);
         }));
         return LEY_OK;
     }
-    LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+    LaunchCfg cf{fin_grid(sms, KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
     LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
     return LEY_OK;
 }
@@ -380,7 +411,7 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
         if (s != LEY_OK) return s;
     }
     if (a.mode == MODE_PARTITION) {
-        const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
+        const LaunchCfg cp{pass_grid(sms), kPassThreads, kernel_smem(KK_PASS), st};
         const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
         LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, 0); }));
         LEY_TRY(launch("classify", st, [&] { return launch_classify_partition(st, w); }));
@@ -440,13 +471,13 @@ static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_
         if (t != LEY_OK) return t;
         if (pairs || fuse) {
             const KernelKind fk = pairs ? KK_FINISH_PAIRS : KK_FINISH_GATHER;
-            LaunchCfg cf{sms * blocks_per_sm(fk), kFinThreads, kernel_smem(fk), st};
+            LaunchCfg cf{fin_grid(sms, fk), kFinThreads, kernel_smem(fk), st};
             LEY_TRY(launch("finish_gather", st, [&] {
                 return launch_batch_finish(cf, w, ks, dreqs, tile_req, pairs);
             }));
             return LEY_OK;
         }
-        LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
         LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
         LEY_TRY(launch("gather", st, [&] {
             return launch_batch_gather_generic(st, sms * blocks_per_sm(KK_GATHER_GENERIC), dreqs,
@@ -1221,6 +1252,113 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
     return LEY_OK;
 }
 
+ley_status ley_get_tuning(ley_tuning* t) {
+    if (!t) return LEY_EINVAL;
+    const Tuning c = cur_tuning();
+    t->big_bucket = c.big;
+    t->tiny_bucket = c.tiny;
+    t->finish_ctas_per_sm = c.fin_ctas;
+    t->pass_ctas_per_sm = c.pass_ctas;
+    return LEY_OK;
+}
+
+ley_status ley_set_tuning(const ley_tuning* t) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return LEY_ECUDA;
+    Tuning c;
+    if (t) {
+        if (t->big_bucket < 256 || t->big_bucket > (uint32_t)kSmall) return LEY_EINVAL;
+        if (t->tiny_bucket < (uint32_t)kTiny || t->tiny_bucket > (uint32_t)kWarpMax) return LEY_EINVAL;
+        if (t->finish_ctas_per_sm > 64 || t->pass_ctas_per_sm > 64) return LEY_EINVAL;
+        c.big = t->big_bucket;
+        c.tiny = t->tiny_bucket;
+        c.fin_ctas = t->finish_ctas_per_sm;
+        c.pass_ctas = t->pass_ctas_per_sm;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune[d] = c;
+    return LEY_OK;
+}
+
+ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                                uint64_t seed, ley_tuning* best) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
+        return LEY_EUNSUPPORTED;
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEY_ECUDA;
+    const ull bytes = n * rec_bytes;
+    void *in = nullptr, *out = nullptr;
+    ley_status s = LEY_OK;
+    if (!scratch_alloc(ds, &in, align_up(bytes, 256), st) ||
+        !scratch_alloc(ds, &out, align_up(bytes, 256), st))
+        s = LEY_ENOMEM;
+    if (s == LEY_OK && launch_fill_random(st, static_cast<uint8_t*>(in), bytes, seed) != cudaSuccess)
+        s = LEY_ECUDA;
+    const Tuning saved = cur_tuning();
+    // Algorithm 1's two thresholds and the CTAs per SM of the two heaviest
+    // kernels; the first candidate is the default.
+    std::vector<Tuning> cands;
+    for (uint32_t big : {2048u, 1536u, 1024u})
+        for (uint32_t tiny : {32u, 64u, 128u})
+            for (uint32_t fc : {0u, 3u}) {
+                Tuning c;
+                c.big = big;
+                c.tiny = tiny;
+                c.fin_ctas = fc;
+                cands.push_back(c);
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == LEY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        s = LEY_ECUDA;
+    float best_ms = 1e30f;
+    Tuning best_t = cands[0];
+    for (size_t i = 0; i < cands.size() && s == LEY_OK; i++) {
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            int d = 0;
+            cudaGetDevice(&d);
+            g_tune[d] = cands[i];
+        }
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && s == LEY_OK; rep++) {  // first run warms up
+            cudaEventRecord(e0, st);
+            s = ley_sort_records(in, out, n, rec_bytes, key_bytes, 0, st);
+            cudaEventRecord(e1, st);
+            if (s == LEY_OK && cudaEventSynchronize(e1) != cudaSuccess) s = LEY_ECUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        if (s == LEY_OK && ms < best_ms) {
+            best_ms = ms;
+            best_t = cands[i];
+        }
+    }
+    if (s == LEY_OK) s = ley_last_device_status(st);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        int d = 0;
+        cudaGetDevice(&d);
+        g_tune[d] = s == LEY_OK ? best_t : saved;
+    }
+    if (best) {
+        best->big_bucket = best_t.big;
+        best->tiny_bucket = best_t.tiny;
+        best->finish_ctas_per_sm = best_t.fin_ctas;
+        best->pass_ctas_per_sm = best_t.pass_ctas;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (in) cudaFreeAsync(in, st);
+    if (out) cudaFreeAsync(out, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return s;
+}
+
 ley_status ley_release_cache(void) {
     {
         std::lock_guard<std::mutex> lk(g_host_scratch_mu);
@@ -1371,7 +1509,7 @@ static NoAllocDev* noalloc_setup() {
 static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const Layout& L,
                                           cudaStream_t st, int sms, uint32_t* err) {
     Work w = make_work(base, L, a.n, err);
-    const KeySpec ks = record_keyspec(a.kb);
+    const KeySpec ks = record_keyspec(a.kb, Tuning{});  // fixed scratch: default thresholds
     LEY_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), st));
     LEY_TRY(cudaMemsetAsync(w.diff[0], 0, sizeof(Diff), st));
     LEY_TRY(cudaMemsetAsync(w.status, 0, L.cap_chunks * kRadix * sizeof(ull), st));
@@ -1417,7 +1555,7 @@ extern "C" ley_status ley_sort_records_noalloc(const void* in, void* out, uint64
     if (!aligned16(in) || !aligned16(out)) return LEY_EINVAL;
     NoAllocDev* dev = noalloc_setup();
     if (!dev) return LEY_ECUDA;
-    const Layout L = make_layout(n, true);
+    const Layout L = make_layout(n, true, kSmall);
     if (L.total + kNoAllocStatusBytes > kNoAllocBytes) return LEY_ENOMEM;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t* err = reinterpret_cast<uint32_t*>(dev->base + kNoAllocBytes - kNoAllocStatusBytes);

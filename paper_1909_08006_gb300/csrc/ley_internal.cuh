@@ -114,6 +114,8 @@ struct KeySpec {
     int ndig;             // number of key bytes (digits)
     unsigned long long hi_mask;  // key bits of (y:x)
     uint32_t lo_mask;     // key bits of z (0 for key/payload pairs)
+    uint32_t big;         // buckets above this many tuples are scattered again (<= kSmall)
+    uint32_t tiny;        // sub-buckets up to this many are ranked by comparison (kTiny..kWarpMax)
 };
 
 // Device views of the scratch workspace of one internal sort.

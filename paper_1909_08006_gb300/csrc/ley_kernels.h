@@ -82,6 +82,9 @@ cudaError_t launch_batch_gather_generic(cudaStream_t s, int grid, const BatchReq
 // dst[0, bytes) = src (host), stream-ordered through kernel parameters (no
 // host buffer needs to outlive the call; capturable in a CUDA graph).
 cudaError_t launch_upload(cudaStream_t s, void* dst, const void* src, size_t bytes);
+// p[0, bytes) = uniform random bytes from `seed` (8-byte aligned p).
+cudaError_t launch_fill_random(cudaStream_t s, uint8_t* p, unsigned long long bytes,
+                               unsigned long long seed);
 cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsigned long long n,
                                  uint32_t* order_out, unsigned long long* hist_out);
 

@@ -168,6 +168,29 @@ cudaError_t launch_upload(cudaStream_t s, void* dst, const void* src, size_t byt
     return cudaSuccess;
 }
 
+// Uniform random bytes (SplitMix64 of the 8-byte word index and a seed), for
+// tuning runs.
+__global__ void k_fill_random(uint8_t* p, ull bytes, ull seed) {
+    const ull words = bytes / 8;
+    for (ull i = (ull)blockIdx.x * blockDim.x + threadIdx.x; i < (bytes + 7) / 8;
+         i += (ull)gridDim.x * blockDim.x) {
+        ull z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        if (i < words) {
+            reinterpret_cast<ull*>(p)[i] = z;
+        } else {
+            for (ull b = i * 8; b < bytes; b++) p[b] = (uint8_t)(z >> (8 * (b - i * 8)));
+        }
+    }
+}
+
+cudaError_t launch_fill_random(cudaStream_t s, uint8_t* p, ull bytes, ull seed) {
+    k_fill_random<<<1024, 256, 0, s>>>(p, bytes, seed);
+    return cudaGetLastError();
+}
+
 // Copies the tuples' input positions (the w field) out as the permutation.
 __global__ void k_tuple_index(const uint4* __restrict__ t, uint32_t* __restrict__ perm, ull n) {
     for (ull i = (ull)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (ull)gridDim.x * blockDim.x)

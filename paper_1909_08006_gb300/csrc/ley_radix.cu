@@ -718,7 +718,7 @@ k_classify(Work w, KeySpec ks, int L) {
     for (uint32_t s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < nseg; s += warps) {
         const Seg sg = w.segs[p][s];
         if (lane == 0) w.seg_pass[p][s] = kNoPass;
-        if (sg.count <= (uint32_t)kSmall) {
+        if (sg.count <= ks.big) {
             if (lane == 0) emit_fin(w, sg.start, sg.count, sg.digit, sg.buf, 0);
             continue;
         }
@@ -774,7 +774,7 @@ k_classify(Work w, KeySpec ks, int L) {
         uint32_t nbig = 0, tbig = 0;
 #pragma unroll
         for (int k = 0; k < 8; k++)
-            if (c8[k] > (uint32_t)kSmall) {
+            if (c8[k] > ks.big) {
                 nbig++;
                 tbig += ceil_div_u64(c8[k], kPassTile);
             }
@@ -801,7 +801,7 @@ k_classify(Work w, KeySpec ks, int L) {
             const int q = (L + 1) & 1;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                if (c8[k] <= (uint32_t)kSmall) continue;
+                if (c8[k] <= ks.big) continue;
                 const uint32_t nt = ceil_div_u64(c8[k], kPassTile);
                 if (slot >= w.cap_seg || tile + nt > w.cap_tiles) {
                     LEY_FAIL(w.err, kErrCapacity);
@@ -827,7 +827,7 @@ k_classify(Work w, KeySpec ks, int L) {
         } else {
 #pragma unroll
             for (int k = 0; k < 8; k++)
-                if (c8[k] > (uint32_t)kSmall) emit_fin(w, sg.start + off8[k], c8[k], ks.ndig, nb, 1);
+                if (c8[k] > ks.big) emit_fin(w, sg.start + off8[k], c8[k], ks.ndig, nb, 1);
         }
         // Runs of small sub-buckets are packed greedily into finishing tasks
         // (lane 0 walks the bins in shared memory, the warp then reserves all
@@ -842,7 +842,7 @@ k_classify(Work w, KeySpec ks, int L) {
             for (int v = 0; v < kRadix; v++) {
                 const uint32_t c = cs[v];
                 if (c == 0) continue;
-                if (c > (uint32_t)kSmall || (g_count && g_count + c > (uint32_t)kSmall)) {
+                if (c > ks.big || (g_count && g_count + c > ks.big)) {
                     if (g_count) {
                         sh_gs[threadIdx.x >> 5][ng] = g_start;
                         sh_gc[threadIdx.x >> 5][ng] = (g_count << 1) | (g_nb == 1 ? 1u : 0u);
@@ -851,7 +851,7 @@ k_classify(Work w, KeySpec ks, int L) {
                     g_count = 0;
                     g_nb = 0;
                 }
-                if (c <= (uint32_t)kSmall) {
+                if (c <= ks.big) {
                     if (g_count == 0) g_start = off;
                     g_count += c;
                     g_nb++;
@@ -1270,7 +1270,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         const uint32_t sc = S.sb_cnt[tid];
         const uint32_t s2 = r0 + S.sb_off[tid];
         if (sc > (uint32_t)kWarpMax) stack_push(S, s2, sc, ds + 1, err);
-        else if (sc > (uint32_t)kTiny) queue_push(S, s2, sc, ds + 1, err);
+        else if (sc > ks.tiny) queue_push(S, s2, sc, ds + 1, err);
     }
 #ifdef LEY_PHASE_TIMING
     if (FROM_GLOBAL && threadIdx.x == 0) atomicAdd(&g_ley_phase[21], (unsigned long long)clock64());
@@ -1280,7 +1280,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         const uint4 tv = B[r0 + i];
         const uint32_t dd = digit_of(tv, ds);
         const uint32_t sc = S.sb_cnt[dd];
-        if (sc <= (uint32_t)kTiny) {
+        if (sc <= ks.tiny) {
             const uint32_t so = r0 + S.sb_off[dd];
             const uint32_t r = cmp_rank(B, so, sc, tv, ks.lo_mask);
             if (r < sc) S.order[so + r] = (uint16_t)(r0 + i);
@@ -1365,12 +1365,12 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < 8; k++)
-        if (c8[k] > (uint32_t)kTiny) queue_push(S, s + off[lane * 8 + k], c8[k], ds + 1, err);
+        if (c8[k] > ks.tiny) queue_push(S, s + off[lane * 8 + k], c8[k], ds + 1, err);
     for (uint32_t i = lane; i < c; i += 32) {
         const uint4 tv = B[s + i];
         const uint32_t dd = digit_of(tv, ds);
         const uint32_t sc = cnt[dd];
-        if (sc <= (uint32_t)kTiny) {
+        if (sc <= ks.tiny) {
             const uint32_t so = s + off[dd];
             const uint32_t r = cmp_rank(B, so, sc, tv, ks.lo_mask);
             if (r < sc) S.order[so + r] = (uint16_t)(s + i);

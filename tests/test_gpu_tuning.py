@@ -1,0 +1,87 @@
+"""The sort's tunables (Algorithm 1's big- and tiny-bucket thresholds, CTAs
+per SM) never change a result: byte-exact parity with the oracle under a
+range of tunings, and the autotuner picks one of its candidates."""
+import numpy as np
+import pytest
+
+import datagen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ley():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_08006_gb300 import build
+    build.build()
+    import paper_1909_08006_gb300 as m
+    yield m
+    m.ley_set_tuning(None)
+
+
+TUNINGS = [
+    {"big_bucket": 256, "tiny_bucket": 32},
+    {"big_bucket": 1024, "tiny_bucket": 128, "finish_ctas_per_sm": 1},
+    {"big_bucket": 2048, "tiny_bucket": 256, "pass_ctas_per_sm": 1},
+    {"big_bucket": 777, "tiny_bucket": 33, "finish_ctas_per_sm": 3, "pass_ctas_per_sm": 1},
+]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_tunings_never_change_results(orc, ley, tuning):
+    ley.ley_set_tuning(tuning)
+    try:
+        assert ley.ley_get_tuning()["big_bucket"] == tuning["big_bucket"]
+        for kind, n in [("uniform", 300_001), ("skew", 200_000), ("few_distinct", 70_000),
+                        ("equal", 50_000), ("prefix_shared", 90_000)]:
+            if kind == "uniform":
+                rec = datagen.uniform_records(n, seed=n)
+            elif kind == "skew":
+                rec = datagen.skew_records(n, seed=2)
+            else:
+                rec = datagen.edge_records(kind, n, seed=5)
+            d_in = rec.to(DEV)
+            d_out = torch.empty_like(d_in)
+            ley.ley_sort_records(d_in, d_out)
+            assert ley.ley_last_device_status() == ley.LEY_OK
+            assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(rec.numpy())), kind
+        keys, idx = datagen.narrow_pairs(100_003, seed=3, distinct=300)
+        ko = torch.empty(keys.shape, dtype=torch.int64, device=DEV)
+        io = torch.empty(idx.shape, dtype=torch.int32, device=DEV)
+        ley.ley_sort_keys_index(keys.to(DEV), idx.to(DEV), ko, io)
+        wk, wi = orc.sort_keys_index(keys.numpy(), idx.numpy())
+        assert np.array_equal(ko.cpu().numpy().view(np.uint64), wk)
+        assert np.array_equal(io.cpu().numpy().view(np.uint32), wi)
+    finally:
+        ley.ley_set_tuning(None)
+
+
+def test_invalid_tunings_rejected(ley):
+    for bad in [{"big_bucket": 100}, {"big_bucket": 4096}, {"tiny_bucket": 8},
+                {"tiny_bucket": 512}, {"finish_ctas_per_sm": 1000}]:
+        with pytest.raises(ley.LeyError) as e:
+            ley.ley_set_tuning(bad)
+        assert e.value.status == ley.LEY_EINVAL
+    ley.ley_set_tuning(None)
+    assert ley.ley_get_tuning() == {"big_bucket": 2048, "tiny_bucket": 32,
+                                    "finish_ctas_per_sm": 0, "pass_ctas_per_sm": 0}
+
+
+def test_autotuner_picks_a_candidate_and_stays_exact(orc, ley):
+    try:
+        best = ley.ley_autotune_records(2_000_000)
+        assert best["big_bucket"] in (2048, 1536, 1024)
+        assert best["tiny_bucket"] in (32, 64, 128)
+        assert best["finish_ctas_per_sm"] in (0, 3)
+        assert ley.ley_get_tuning() == best
+        rec = datagen.skew_records(250_000, seed=8)
+        d_in = rec.to(DEV)
+        d_out = torch.empty_like(d_in)
+        ley.ley_sort_records(d_in, d_out)
+        assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(rec.numpy()))
+    finally:
+        ley.ley_set_tuning(None)
