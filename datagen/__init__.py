@@ -208,7 +208,7 @@ def edge_records(kind: str, n: int, seed: int, rec_bytes: int = 100,
     if n == 0:
         return rec
     if kind == "equal":
-        rec[:, :kb] = rec[0, :kb]
+        rec[:, :kb] = rec[0, :kb].clone()
     elif kind in ("sorted", "reversed"):
         i = torch.arange(n, dtype=torch.int64, device=device)
         if kind == "reversed":
@@ -228,6 +228,29 @@ def edge_records(kind: str, n: int, seed: int, rec_bytes: int = 100,
         rec[:, :kb - 2] = 0x7E
     else:
         raise ValueError(f"unknown edge kind {kind!r}")
+    return rec
+
+
+def ascii_records(n: int, seed: int, rec_bytes: int = 100, key_bytes: int = 10,
+                  shared_prefix: int = 0, alphabet: int = 95, dup_frac: float = 0.0,
+                  device="cpu") -> torch.Tensor:
+    """Records with printable ASCII keys, like the Sort Benchmark's ASCII
+    records (the paper's 20 GB set): key bytes are drawn from the first
+    ``alphabet`` printable characters (0x20..); the first ``shared_prefix``
+    key bytes are the same for every record; a ``dup_frac`` fraction of the
+    records (every k-th) copies the whole key of the record before it.  The
+    value bytes stay uniform."""
+    rec = uniform_records(n, seed, rec_bytes, device)
+    if n == 0:
+        return rec
+    kb = key_bytes
+    rec[:, :kb] = (0x20 + (rec[:, :kb].to(torch.int64) % alphabet)).to(torch.uint8)
+    if shared_prefix:
+        rec[:, :shared_prefix] = rec[0, :shared_prefix].clone()
+    step = max(1, int(round(1.0 / dup_frac))) if dup_frac > 0 else 0
+    if step and n > step:
+        idx = torch.arange(step, n, step, device=device)
+        rec[idx, :kb] = rec[idx - 1, :kb]
     return rec
 
 

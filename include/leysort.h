@@ -70,7 +70,14 @@ typedef void* ley_stream_t;
  *               the sorted records are in `out`.  Any other combination
  *               (mixed, pageable host memory) is LEY_EINVAL.
  *   rec_bytes   4..4096, a multiple of 4 (100 takes the specialised kernels).
- *   key_bytes   1..12 and <= rec_bytes; the key is at offset 0.
+ *   key_bytes   1..rec_bytes; the key is at offset 0.  A (key, pointer) tuple
+ *               holds 12 key bytes, so a longer key is sorted one 12-byte
+ *               window at a time, least significant window first
+ *               (ceil(key_bytes / 12) sorts, each stable on the order left by
+ *               the windows after it); scratch grows by 12 bytes per record.
+ *               Long keys are supported for device buffers and in the partial
+ *               host mode; where the external mode would be needed,
+ *               LEY_EUNSUPPORTED.
  *   mem_budget  cap on the library's device allocations in bytes, 0 = none.
  *   n           < 2^32.  n == 0 returns LEY_OK without touching the buffers.
  */

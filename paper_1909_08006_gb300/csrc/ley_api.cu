@@ -490,9 +490,68 @@ static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_
     return s;
 }
 
+// ------------------------------------------------- keys longer than 12 bytes
+
+// The tuple holds 12 key bytes.  A longer key is sorted window by window,
+// least significant 12-byte window first; each window is one full MSD sort
+// of (window, position in the order so far), so equal windows keep the order
+// of the windows after them, and the composed order is the stable order of
+// the whole key.  ceil(key_bytes / 12) sorts; `ord` holds two n-entry
+// arrays; the final order is returned in *result.
+static constexpr uint32_t kWindow = 12;
+
+static ley_status enqueue_long_key_order(const SortArgs& a, const Work& w, const Layout& L,
+                                         uint32_t* const ord[2], cudaStream_t st, int sms,
+                                         const uint32_t** result) {
+    const uint32_t W = (a.kb + kWindow - 1) / kWindow;
+    const uint32_t* cur = nullptr;
+    int nb = 0;
+    for (int i = (int)W - 1; i >= 0; i--) {
+        const uint32_t koff = kWindow * (uint32_t)i;
+        const uint32_t wl = std::min(kWindow, a.kb - koff);
+        const KeySpec ks = record_keyspec(wl);
+        ley_status s = stage_prepare(w, L, st, a.n, 0);
+        if (s != LEY_OK) return s;
+        LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
+        LEY_TRY(launch("extract", st, [&] {
+            return launch_extract_window(c, a.in, cur, a.n, a.rec, koff, ks, w);
+        }));
+        SortArgs b = a;
+        b.kb = wl;
+        s = stage_levels_finish(b, w, ks, st, sms, false);
+        if (s != LEY_OK) return s;
+        uint32_t* next = ord[nb];
+        LEY_TRY(launch("compose", st, [&] {
+            return launch_compose_order(st, sms * 4, cur, w.perm, next, a.n, w.err);
+        }));
+        cur = next;
+        nb ^= 1;
+    }
+    *result = cur;
+    return LEY_OK;
+}
+
+static size_t long_key_extra(ull n) { return 2 * align_up(n * sizeof(uint32_t), 256); }
+
 static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
+    if (a.mode == MODE_RECORDS && a.kb > kWindow) {
+        const Layout L = make_layout(a.n, true);
+        const size_t total = L.total + long_key_extra(a.n);
+        if (budget && total > budget) return LEY_ENOMEM;
+        void* base = nullptr;
+        if (!scratch_alloc(ds, &base, total, st)) return LEY_ENOMEM;
+        char* b = static_cast<char*>(base);
+        Work w = make_work(b, L, a.n, ds->err);
+        uint32_t* ord[2] = {reinterpret_cast<uint32_t*>(b + L.total),
+                            reinterpret_cast<uint32_t*>(b + L.total + long_key_extra(a.n) / 2)};
+        const uint32_t* order = nullptr;
+        ley_status s = enqueue_long_key_order(a, w, L, ord, st, ds->sms, &order);
+        if (s == LEY_OK) s = stage_gather(a, order, st, ds->sms, 0, a.n, a.out);
+        cudaFreeAsync(base, st);
+        return s;
+    }
     const Layout L = make_layout(a.n, a.mode == MODE_RECORDS && !fused_gather(a.rec));
     if (budget && L.total > budget) return LEY_ENOMEM;
     void* base = nullptr;
@@ -651,9 +710,11 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
     if (!ds) return LEY_ECUDA;
     const ull bytes = a.n * a.rec;
     const Layout L = make_layout(a.n, true);
+    const bool long_key = a.kb > kWindow;
     const ull q = staging_records(a.n, a.rec, budget);
     const size_t stg_bytes = align_up(q * a.rec, 256);
-    const size_t need = align_up(bytes, 256) + L.total + kStaging * stg_bytes;
+    const size_t need = align_up(bytes, 256) + L.total + kStaging * stg_bytes +
+                        (long_key ? long_key_extra(a.n) : 0);
     if (budget && need > budget) return LEY_ENOMEM;
     void* dmem = nullptr;
     if (!scratch_alloc(ds, &dmem, need, st)) return LEY_ENOMEM;
@@ -670,14 +731,28 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         Work w = make_work(ws, L, a.n, ds->err);
         const KeySpec ks = record_keyspec(a.kb);
         hp.mark(hp.h2d, "in begin");
-        if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
-        if (s == LEY_OK) s = stream_in_extract(d, a.in, reinterpret_cast<uint8_t*>(din), w, ks, st, hp, ds->sms);
-        hp.mark(hp.h2d, "in end");
-        hp.mark(st, "extracted");
-        if (s == LEY_OK) s = stage_levels_finish(d, w, ks, st, ds->sms);
+        const uint32_t* order = w.perm;
+        if (long_key) {
+            // the whole input first, then one sort per 12-byte key window
+            if (s == LEY_OK && cudaMemcpyAsync(din, a.in, bytes, cudaMemcpyHostToDevice, hp.h2d) !=
+                                   cudaSuccess)
+                s = LEY_ECUDA;
+            if (s == LEY_OK && !hp.order(hp.h2d, st)) s = LEY_ECUDA;
+            hp.mark(hp.h2d, "in end");
+            uint32_t* ord[2] = {reinterpret_cast<uint32_t*>(ws + L.total + kStaging * stg_bytes),
+                                reinterpret_cast<uint32_t*>(ws + L.total + kStaging * stg_bytes +
+                                                            long_key_extra(a.n) / 2)};
+            if (s == LEY_OK) s = enqueue_long_key_order(d, w, L, ord, st, ds->sms, &order);
+        } else {
+            if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
+            if (s == LEY_OK) s = stream_in_extract(d, a.in, reinterpret_cast<uint8_t*>(din), w, ks, st, hp, ds->sms);
+            hp.mark(hp.h2d, "in end");
+            hp.mark(st, "extracted");
+            if (s == LEY_OK) s = stage_levels_finish(d, w, ks, st, ds->sms);
+        }
         hp.mark(st, "sorted");
         cudaEvent_t stg_free[kStaging] = {};
-        if (s == LEY_OK) s = stream_out(d, w.perm, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
+        if (s == LEY_OK) s = stream_out(d, order, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
         hp.mark(st, "gathered");
         hp.mark(hp.d2h, "out end");
         if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
@@ -991,6 +1066,7 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
 static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st) {
     ley_status s = run_host_partial(a, budget, st);
     if (s != LEY_ENOMEM || !budget) return s;
+    if (a.kb > kWindow) return LEY_EUNSUPPORTED;  // the merge compares 12-byte tuples
     return run_host_external(a, budget, st);
 }
 
@@ -1063,7 +1139,7 @@ extern "C" {
 
 ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
                             uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 4 ||
         rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     if (n == 0) return LEY_OK;
@@ -1245,9 +1321,13 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
 ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
                                uint64_t* bytes) {
     if (!bytes) return LEY_EINVAL;
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 4 ||
         rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
+    if (key_bytes > kWindow) {
+        *bytes = n ? make_layout(n, true).total + long_key_extra(n) : 0;
+        return LEY_OK;
+    }
     *bytes = n ? make_layout(n, !fused_gather(rec_bytes)).total : 0;
     return LEY_OK;
 }

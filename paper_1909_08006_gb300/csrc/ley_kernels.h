@@ -64,6 +64,15 @@ cudaError_t launch_gather(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
 cudaError_t launch_gather_err(const LaunchCfg& c, const uint8_t* in, uint8_t* out,
                               const uint32_t* perm, unsigned long long n, unsigned long long n_in,
                               uint32_t rec_bytes, int variant, uint32_t* err);
+// Keys longer than 12 bytes: tuples of the 12-byte window at koff of record
+// order[j] (identity if order is null), carrying j; and the composition
+// next[j] = order[pass[j]] (pass[j] if order is null).
+cudaError_t launch_extract_window(const LaunchCfg& c, const uint8_t* in, const uint32_t* order,
+                                  unsigned long long n, uint32_t rec, uint32_t koff, KeySpec ks,
+                                  const Work& w);
+cudaError_t launch_compose_order(cudaStream_t s, int grid, const uint32_t* order,
+                                 const uint32_t* pass, uint32_t* next, unsigned long long n,
+                                 uint32_t* err);
 // Batched sorts (requests back to back in one tuple space, see BatchReq).
 cudaError_t launch_batch_setup(cudaStream_t s, const BatchReq* reqs, uint32_t R, const Work& w,
                                uint32_t* tile_req, uint32_t ntiles, int digit0);

@@ -101,9 +101,10 @@ __device__ __forceinline__ uint32_t sel8(const uint32_t (&w)[8], uint32_t q) {
 // granules.
 template <int REC>
 __device__ __forceinline__ uint4 load_record_key(const uint8_t* __restrict__ in, ull i,
-                                                 uint32_t rec_rt, uint32_t kb, const KeySpec& ks) {
+                                                 uint32_t rec_rt, uint32_t kb, const KeySpec& ks,
+                                                 uint32_t koff = 0) {
     const uint32_t rec = REC ? (uint32_t)REC : rec_rt;
-    ull s = i * rec;
+    ull s = i * rec + koff;  // the key (window) starts koff bytes into the record
     const uint4* p = reinterpret_cast<const uint4*>(in + (s & ~15ull));
     uint32_t o = (uint32_t)(s & 15);
     uint4 c0 = __ldg(p);
@@ -235,6 +236,71 @@ k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpe
     warp_or_diff(dhi, dlo, sh_d);
     __syncthreads();
     if (threadIdx.x == 0) flush_diff(sh_d, w.diff[0]);
+}
+
+// Keys longer than 12 bytes are sorted window by window, least significant
+// 12-byte window first (LSD over windows, each window sorted by the MSD
+// machinery): tuple j holds window [koff, koff + 12) of record order[j] --
+// the order produced by the windows after this one (identity for the last
+// window) -- and carries j, so that equal windows keep that order.
+__global__ void __launch_bounds__(256)
+k_extract_window(const uint8_t* __restrict__ in, const uint32_t* __restrict__ order, ull n,
+                 uint32_t rec, uint32_t koff, KeySpec ks, Work w, uint32_t* err) {
+    __shared__ uint32_t sh_hist[kRadix];
+    __shared__ uint32_t sh_d[3];
+    if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t kb = (uint32_t)ks.ndig;
+    const uint32_t r0 = order ? order[0] : 0u;
+    const uint4 ref = load_record_key<0>(in, r0 < n ? r0 : 0, rec, kb, ks, koff);
+    uint4* __restrict__ tup = w.tup[0];
+    ull dhi = 0;
+    uint32_t dlo = 0;
+    const uint32_t ntiles = ceil_div_u64(n, kPassTile);
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();
+        sh_hist[threadIdx.x] = 0;
+        __syncthreads();
+        const ull base = (ull)t * kPassTile;
+#pragma unroll 1
+        for (int k = 0; k < kPassTile / 256; k++) {
+            const ull i = base + k * 256 + threadIdx.x;
+            uint32_t dg = 256u;
+            if (i < n) {
+                uint32_t r = order ? order[i] : (uint32_t)i;
+                if (r >= n) {  // never for a valid order; keeps reads in bounds
+                    LEY_FAIL(err, kErrCapacity);
+                    r = 0;
+                }
+                uint4 tv = load_record_key<0>(in, r, rec, kb, ks, koff);
+                tv.w = (uint32_t)i;
+                tup[i] = tv;
+                dg = digit_of(tv, 0);
+                dhi |= key_hi(tv) ^ key_hi(ref);
+                dlo |= tv.z ^ ref.z;
+            }
+            hist_add_vote(sh_hist, dg);
+        }
+        __syncthreads();
+        w.tile_cnt[(ull)t * kRadix + threadIdx.x] = sh_hist[threadIdx.x];
+        if (threadIdx.x == 0) w.seg_tile_owner[0][t] = 0;
+    }
+    warp_or_diff(dhi, dlo, sh_d);
+    __syncthreads();
+    if (threadIdx.x == 0) flush_diff(sh_d, w.diff[0]);
+}
+
+// next[j] = order ? order[pass[j]] : pass[j]: the order after one more window.
+__global__ void k_compose_order(const uint32_t* __restrict__ order, const uint32_t* __restrict__ pass,
+                                uint32_t* __restrict__ next, ull n, uint32_t* err) {
+    for (ull j = (ull)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (ull)gridDim.x * blockDim.x) {
+        uint32_t p = pass[j];
+        if (p >= n) {
+            LEY_FAIL(err, kErrCapacity);
+            p = 0;
+        }
+        next[j] = order ? order[p] : p;
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -1656,6 +1722,19 @@ extern "C" int ley_phase_read(unsigned long long* out) {
 }
 namespace ley {
 #endif
+
+cudaError_t launch_extract_window(const LaunchCfg& c, const uint8_t* in, const uint32_t* order,
+                                  ull n, uint32_t rec, uint32_t koff, KeySpec ks, const Work& w) {
+    const int grid = (int)min((uint32_t)c.grid, ceil_div_u64(n, kPassTile));
+    k_extract_window<<<grid, 256, 0, c.stream>>>(in, order, n, rec, koff, ks, w, w.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compose_order(cudaStream_t s, int grid, const uint32_t* order,
+                                 const uint32_t* pass, uint32_t* next, ull n, uint32_t* err) {
+    k_compose_order<<<grid, 256, 0, s>>>(order, pass, next, n, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_setup(cudaStream_t s, const BatchReq* reqs, uint32_t R, const Work& w,
                                uint32_t* tile_req, uint32_t ntiles, int digit0) {

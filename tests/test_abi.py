@@ -52,8 +52,10 @@ def test_host_only_entry_points(ley):
     b104 = ley.ley_workspace_bytes(100_000_000, rec_bytes=104)
     assert b104 - b == 4 * 100_000_000
     with pytest.raises(ley.LeyError) as e:
-        ley.ley_workspace_bytes(10, rec_bytes=100, key_bytes=13)
+        ley.ley_workspace_bytes(10, rec_bytes=100, key_bytes=101)
     assert e.value.status == ley.LEY_EUNSUPPORTED
+    # keys longer than 12 bytes: a permutation and two order arrays more
+    assert ley.ley_workspace_bytes(100_000_000, key_bytes=30) > b + 12 * 100_000_000 - 1
     with pytest.raises(ley.LeyError):
         ley.ley_workspace_bytes(10, rec_bytes=102, key_bytes=10)
 

@@ -199,8 +199,8 @@ def test_pinned_host_records_exact(orc, ley):
 def test_error_codes(ley):
     rec = datagen.uniform_records(1000, seed=1).to(DEV)
     out = torch.empty_like(rec)
-    with pytest.raises(ley.LeyError) as e:
-        ley.ley_sort_records(rec, out, key_bytes=13)
+    with pytest.raises(ley.LeyError) as e:  # key longer than the record
+        ley.ley_sort_records(rec, out, key_bytes=101)
     assert e.value.status == ley.LEY_EUNSUPPORTED
     with pytest.raises(ley.LeyError) as e:  # overlapping output
         ley.ley_sort_records(rec, rec, key_bytes=10)
