@@ -208,13 +208,17 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         return run_batch(args, world, rank, dev, stream, pg)
     if wl == "serve":
         return run_serve(args, world, rank, dev, stream, pg)
-    gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
-    d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
+    kb = args.key_bytes
+    if wl == "ascii":  # printable keys, like the Sort Benchmark's ASCII records
+        d_in = datagen.ascii_records(n, seed=6, key_bytes=kb, device=dev)
+    else:
+        gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
+        d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
     d_out = torch.empty_like(d_in)
     torch.cuda.synchronize()
 
     def step():
-        ley.ley_sort_records(d_in, d_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+        ley.ley_sort_records(d_in, d_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -283,11 +287,11 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         del d_in
         torch.cuda.empty_cache()
         h_out = torch.empty_like(h_in).pin_memory()
-        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
         barrier(pg, dev)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, stream=stream)
+            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
         dt = (time.perf_counter() - t0) / args.e2e_steps
         dt = max_over_ranks(dt, pg, dev)
         e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
@@ -304,11 +308,13 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
 
     value = world * n * REC / (ms * 1e-3) / 1e9
     return {
-        "metric": METRIC if wl == "uniform" else f"GB/s of 100-byte records sorted ({wl} keys)", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "metric": (METRIC if wl == "uniform" and kb == KEY
+                   else f"GB/s of 100-byte records sorted ({wl} keys, {kb}-byte key)"),
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded SplitMix64 records shaped like the paper's gensort data)",
-        "config": {"workload": workload, "records": n, "record_bytes": REC, "key_bytes": KEY,
+        "config": {"workload": workload, "records": n, "record_bytes": REC, "key_bytes": kb,
                    "resident": "HBM", "l2": "inputs larger than L2 (10 GB), no flush",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
@@ -725,8 +731,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "skew", "pairs", "partial", "external", "batch",
+                    choices=["uniform", "skew", "ascii", "pairs", "partial", "external", "batch",
                              "serve"])
+    ap.add_argument("--key-bytes", type=int, default=KEY,
+                    help="key length of the uniform/skew/ascii workloads (longer than 12: "
+                         "one sort per 12-byte window)")
     ap.add_argument("--autotune", action="store_true",
                     help="run the library's autotuner on the workload's size first")
     ap.add_argument("--serve-batch", type=int, default=256)
