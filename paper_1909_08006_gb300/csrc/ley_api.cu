@@ -299,6 +299,7 @@ struct SortArgs {
     ull* hist_out;
     ull n;
     uint32_t rec, kb, digit;
+    bool in_host = false;     // records at `in` are pinned host memory mapped for the device
 };
 
 #define LEY_TRY(x)                                   \
@@ -320,10 +321,11 @@ static ley_status stage_prepare(const Work& w, const Layout& L, cudaStream_t st,
 // Records [t_begin, t_end) tiles -> tuples and per-tile digit counts.
 static ley_status stage_extract_records(const SortArgs& a, const Work& w, const KeySpec& ks,
                                         cudaStream_t st, int sms, int digit0, uint32_t t_begin,
-                                        uint32_t t_end) {
+                                        uint32_t t_end, const uint8_t* ref_in = nullptr) {
     LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
     LEY_TRY(launch("extract", st, [&] {
-        return launch_extract_records_tiles(c, a.in, a.n, a.rec, ks, w, digit0, t_begin, t_end);
+        return launch_extract_records_tiles(c, a.in, a.n, a.rec, ks, w, digit0, t_begin, t_end,
+                                            ref_in);
     }));
     return LEY_OK;
 }
@@ -382,7 +384,9 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
 static ley_status stage_gather(const SortArgs& a, const uint32_t* perm, cudaStream_t st, int sms,
                                ull j0, ull j1, uint8_t* out_base) {
     if (j1 <= j0) return LEY_OK;
-    const int gv = a.rec == 100 ? (gather_variant() == 0 ? 0 : 1) : 0;
+    // Records read from host memory (over the host link) take the plain-load
+    // kernel: bulk copies are only used on device memory.
+    const int gv = a.rec == 100 && !a.in_host ? (gather_variant() == 0 ? 0 : 1) : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
@@ -1062,10 +1066,107 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     return s;
 }
 
+// Keys-only external sort: only the (key, pointer) tuples live on the device.
+// The input streams in once (chunks through a two-buffer ring, each chunk's
+// tuples extracted as it lands), the tuples are sorted on the device, and
+// the records are gathered by the final order straight from the pinned host
+// input (the GPU reading host memory over the host link) into staging
+// buffers that stream out.  The link carries n*100 bytes in for the keys,
+// n*100 bytes of record reads and n*100 bytes out -- no run scratch on the
+// host -- and the device holds 36 bytes per record, so it serves inputs up to
+// about budget / 36 records.  Returns LEY_ENOMEM (touching nothing) when the
+// tuples do not fit or the input is not mapped for the device.
+static ley_status run_host_keys_only(const SortArgs& a, ull budget, cudaStream_t st) {
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    if (a.kb > kWindow) return LEY_ENOMEM;
+    void* in_dev = nullptr;
+    if (cudaHostGetDevicePointer(&in_dev, const_cast<uint8_t*>(a.in), 0) != cudaSuccess ||
+        !in_dev) {
+        cudaGetLastError();
+        return LEY_ENOMEM;
+    }
+    const Layout L = make_layout(a.n, true);
+    // chunks of n/8 records (whole tiles), between 64 Ki and 4 Mi records
+    ull chunk = (ull)ceil_div_u64(a.n / 8 + 1, kPassTile) * kPassTile;
+    chunk = std::max<ull>(chunk, 16ull * kPassTile);
+    chunk = std::min<ull>(chunk, 1024ull * kPassTile);
+    const size_t chunk_bytes = align_up(chunk * a.rec, 256);
+    const ull q = staging_records(a.n, a.rec, budget);
+    const size_t stg_bytes = align_up(q * a.rec, 256);
+    const size_t need = L.total + 2 * chunk_bytes + kStaging * stg_bytes;
+    if (budget && need > budget) return LEY_ENOMEM;
+    void* dmem = nullptr;
+    if (!scratch_alloc(ds, &dmem, need, st)) return LEY_ENOMEM;
+    char* ws = static_cast<char*>(dmem);
+    uint8_t* ring[2] = {reinterpret_cast<uint8_t*>(ws + L.total),
+                        reinterpret_cast<uint8_t*>(ws + L.total + chunk_bytes)};
+    uint8_t* stg[kStaging];
+    for (int i = 0; i < kStaging; i++)
+        stg[i] = reinterpret_cast<uint8_t*>(ws + L.total + 2 * chunk_bytes + i * stg_bytes);
+    ley_status s = LEY_OK;
+    {
+        HostPipe hp(st);
+        if (!hp.ok) s = LEY_ECUDA;
+        Work w = make_work(ws, L, a.n, ds->err);
+        const KeySpec ks = record_keyspec(a.kb);
+        if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
+        hp.mark(hp.h2d, "in begin");
+        cudaEvent_t ring_free[2] = {nullptr, nullptr};
+        for (ull c0 = 0, ci = 0; c0 < a.n && s == LEY_OK; c0 += chunk, ci++) {
+            const ull c1 = std::min(c0 + chunk, a.n);
+            const int b = (int)(ci & 1);
+            if (!hp.wait(hp.h2d, ring_free[b])) s = LEY_ECUDA;
+            if (s == LEY_OK && cudaMemcpyAsync(ring[b], a.in + c0 * a.rec, (c1 - c0) * a.rec,
+                                               cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+                s = LEY_ECUDA;
+            if (s == LEY_OK && !hp.order(hp.h2d, st)) s = LEY_ECUDA;
+            // record i of the input sits at ring[b] + (i - c0) * rec
+            SortArgs ca = a;
+            ca.in = ring[b] - c0 * a.rec;
+            // (the difference mask against record 0, read from the host input)
+            if (s == LEY_OK)
+                s = stage_extract_records(ca, w, ks, st, ds->sms, 0, (uint32_t)(c0 / kPassTile),
+                                          ceil_div_u64(c1, kPassTile),
+                                          static_cast<const uint8_t*>(in_dev));
+            if (s == LEY_OK && !(ring_free[b] = hp.record(st))) s = LEY_ECUDA;
+        }
+        hp.mark(hp.h2d, "in end");
+        if (s == LEY_OK) s = stage_levels_finish(a, w, ks, st, ds->sms);
+        hp.mark(st, "sorted");
+        SortArgs ga = a;
+        ga.in = static_cast<const uint8_t*>(in_dev);
+        ga.in_host = true;
+        cudaEvent_t stg_free[kStaging] = {};
+        if (s == LEY_OK) s = stream_out(ga, w.perm, 0, a.n, a.out, stg, q, st, hp, stg_free, ds->sms);
+        hp.mark(st, "gathered");
+        hp.mark(hp.d2h, "out end");
+        if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
+        cudaFreeAsync(dmem, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
+    }
+    return s;
+}
+
+// Which external design to use: the run formation + k-way merge (default),
+// or with LEY_EXTERNAL=keys the keys-only design whenever its tuples fit the
+// budget.  Measured on GB300 at 4e8 records: the keys-only design's gather
+// reads host memory at about 1 GB/s (random 100-byte loads over the host
+// link, latency-bound), 41 s against 0.55 s for the merge design.
+static int external_design() {
+    const char* v = std::getenv("LEY_EXTERNAL");
+    if (v && std::strcmp(v, "keys") == 0) return 1;
+    return 0;
+}
+
 // Host-memory sort: partially in-memory when it fits the budget, else external.
 static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st) {
     ley_status s = run_host_partial(a, budget, st);
     if (s != LEY_ENOMEM || !budget) return s;
+    if (external_design() == 1) {
+        s = run_host_keys_only(a, budget, st);
+        if (s != LEY_ENOMEM) return s;
+    }
     if (a.kb > kWindow) return LEY_EUNSUPPORTED;  // the merge compares 12-byte tuples
     return run_host_external(a, budget, st);
 }

@@ -37,11 +37,14 @@ struct LaunchCfg {
 // of the whole input (list 0, slot 0).
 cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, unsigned long long n,
                                    uint32_t rec_bytes, KeySpec ks, const Work& w, int hist_digit);
-// Same, for tiles [t_begin, t_end) only (kPassTile records each).
+// Same, for tiles [t_begin, t_end) only (kPassTile records each).  The
+// key-difference mask is taken against the key of the record at ref_in
+// (default: record 0 at `in`), which must be the same in every launch over
+// one input.
 cudaError_t launch_extract_records_tiles(const LaunchCfg& c, const uint8_t* in,
                                          unsigned long long n, uint32_t rec_bytes, KeySpec ks,
                                          const Work& w, int hist_digit, uint32_t t_begin,
-                                         uint32_t t_end);
+                                         uint32_t t_end, const uint8_t* ref_in = nullptr);
 cudaError_t launch_extract_pairs(const LaunchCfg& c, const uint64_t* keys, const uint32_t* idx,
                                  unsigned long long n, KeySpec ks, const Work& w);
 cudaError_t launch_init(cudaStream_t s, const Work& w, unsigned long long n, int digit0);

@@ -191,13 +191,15 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool v
 template <int REC>
 __global__ void __launch_bounds__(256)
 k_extract_records(const uint8_t* __restrict__ in, ull n, uint32_t rec_rt, KeySpec ks, Work w,
-                  int hist_digit, uint32_t t_begin, uint32_t t_end) {
+                  int hist_digit, uint32_t t_begin, uint32_t t_end, const uint8_t* ref_in) {
     __shared__ uint32_t sh_hist[kRadix];
     __shared__ uint32_t sh_d[3];
     if (threadIdx.x < 3) sh_d[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t kb = (uint32_t)ks.ndig;
-    const uint4 ref = load_record_key<REC>(in, 0, rec_rt, kb, ks);
+    // The difference mask is taken against one fixed key (record 0 of the
+    // whole input) in every launch over the input's tiles.
+    const uint4 ref = load_record_key<REC>(ref_in, 0, rec_rt, kb, ks);
     uint4* __restrict__ tup = w.tup[0];
     ull dhi = 0;
     uint32_t dlo = 0;
@@ -1791,15 +1793,16 @@ cudaError_t launch_extract_records(const LaunchCfg& c, const uint8_t* in, ull n,
 
 cudaError_t launch_extract_records_tiles(const LaunchCfg& c, const uint8_t* in, ull n,
                                          uint32_t rec, KeySpec ks, const Work& w, int hist_digit,
-                                         uint32_t t_begin, uint32_t t_end) {
+                                         uint32_t t_begin, uint32_t t_end, const uint8_t* ref_in) {
     if (t_end <= t_begin) return cudaSuccess;
+    if (!ref_in) ref_in = in;
     const int grid = (int)min((uint32_t)c.grid, t_end - t_begin);
     if (rec == 100)
         k_extract_records<100><<<grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit, t_begin,
-                                                           t_end);
+                                                           t_end, ref_in);
     else
         k_extract_records<0><<<grid, 256, 0, c.stream>>>(in, n, rec, ks, w, hist_digit, t_begin,
-                                                         t_end);
+                                                         t_end, ref_in);
     return cudaGetLastError();
 }
 

@@ -104,3 +104,18 @@ def test_merge_records_matches_oracle(orc, ley, k, alpha):
     ley.ley_merge_records(d_runs, starts, d_out)
     assert ley.ley_last_device_status() == ley.LEY_OK
     assert np.array_equal(d_out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("n,budget", [(1_000_000, 80 << 20), (600_001, 50 << 20)])
+def test_keys_only_external_sort_exact(orc, ley, monkeypatch, n, budget):
+    # the tuples fit the budget but the records do not: only the keys stay on
+    # the device and the records are gathered from the pinned host input
+    rec = datagen.skew_records(n, seed=n)
+    ws = ley.ley_workspace_bytes(n)
+    assert ws + n * 100 > budget > ws
+    monkeypatch.setenv("LEY_EXTERNAL", "keys")
+    got = host_sort(ley, rec, budget)
+    want = orc.sort_records(rec.numpy())
+    assert np.array_equal(got, want)
+    monkeypatch.setenv("LEY_EXTERNAL", "merge")
+    assert np.array_equal(host_sort(ley, rec, budget), want)
