@@ -1,0 +1,61 @@
+"""The multi-process form of the bench on CPU (gloo, world size 2): the sort
+has no exchange step, so N GPUs run N replicas; the only cross-rank work is
+the barrier and the max-over-ranks timing, and rank 0 alone prints."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        bench.barrier(dist)
+        q.put((rank, bench.max_over_ranks(float(10 + rank), dist)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_barrier_with_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 11.0, 1: 11.0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    # under torchrun every rank runs main(); only rank 0 does the work and
+    # returns the line to print
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(ref_sample=20_000, warmup=3, steps=1, n=100_000_000)
+    assert bench.run_reference(args, world=2, rank=1, pg=None) is None
+    out = bench.run_reference(args, world=2, rank=0, pg=None)
+    json.dumps(out)
+    assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle"
