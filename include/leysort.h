@@ -300,6 +300,17 @@ ley_status ley_last_device_status(ley_stream_t stream);
 ley_status ley_sort_records_noalloc(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
                                     uint32_t key_bytes, ley_stream_t stream);
 
+/*
+ * Failure-detection self-test: launches a kernel whose bounded wait cannot
+ * succeed -- which = 0: a device word that nothing writes (the kind of wait
+ * of the scan's look-back); which = 1: an mbarrier whose bytes no copy
+ * delivers (the kind of wait of the TMA gathers) -- waits for it and returns
+ * the device status it latched, which is LEY_ETIMEOUT when detection works.
+ * The status word is cleared on return and the context stays usable.  Takes
+ * about as long as one wait's limit (a second or less).
+ */
+ley_status ley_selftest_timeout(uint32_t which, ley_stream_t stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t ley_launch_count(void);
 

@@ -26,7 +26,7 @@ __all__ = [
     "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
     "ley_server_create", "ley_server_submit_records", "ley_server_submit_pairs",
     "ley_server_wait", "ley_server_stats", "ley_server_destroy",
-    "ley_get_tuning", "ley_set_tuning", "ley_autotune_records",
+    "ley_get_tuning", "ley_set_tuning", "ley_autotune_records", "ley_selftest_timeout",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -112,6 +112,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_records_batch.restype = ctypes.c_int
     lib.ley_sort_keys_index_batch.argtypes = [ctypes.POINTER(_PairsReq), u32, u64, vp]
     lib.ley_sort_keys_index_batch.restype = ctypes.c_int
+    lib.ley_selftest_timeout.argtypes = [u32, vp]
+    lib.ley_selftest_timeout.restype = ctypes.c_int
     lib.ley_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
     lib.ley_get_tuning.restype = ctypes.c_int
     lib.ley_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -230,6 +232,12 @@ def ley_sort_keys_index_batch(requests, mem_budget: int = 0, stream=None) -> int
         st = _stream(stream)
     return _check(_lib.ley_sort_keys_index_batch(arr, len(requests), mem_budget, st),
                   "ley_sort_keys_index_batch")
+
+
+def ley_selftest_timeout(which: int = 0, stream=None) -> int:
+    """Makes one bounded device wait give up on purpose; returns (does not
+    raise) the status it latched: LEY_ETIMEOUT when detection works."""
+    return int(_lib.ley_selftest_timeout(which, _stream(stream)))
 
 
 # ---------------------------------------------------------------- tuning

@@ -1540,6 +1540,23 @@ ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_byt
     return s;
 }
 
+ley_status ley_selftest_timeout(uint32_t which, ley_stream_t stream) {
+    if (which > 1) return LEY_EINVAL;
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* word = nullptr;
+    if (!scratch_alloc(ds, &word, 256, st)) return LEY_ENOMEM;
+    ley_status s = LEY_OK;
+    if (cudaMemsetAsync(word, 0, 256, st) != cudaSuccess ||
+        launch_selftest_wait(st, which, static_cast<const unsigned long long*>(word), ds->err) !=
+            cudaSuccess)
+        s = LEY_ECUDA;
+    cudaFreeAsync(word, st);
+    const ley_status d = ley_last_device_status(stream);
+    return s != LEY_OK ? s : d;
+}
+
 ley_status ley_release_cache(void) {
     {
         std::lock_guard<std::mutex> lk(g_host_scratch_mu);

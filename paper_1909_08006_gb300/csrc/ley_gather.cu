@@ -208,6 +208,40 @@ k_gather_generic(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
     }
 }
 
+// ------------------------------------------------------- wait self-test
+//
+// Failure detection without a GPU fault: one of the library's bounded waits
+// is made to give up on purpose, against a condition that nothing will ever
+// satisfy -- a device word nobody writes (the scan look-back's kind of wait)
+// or an mbarrier whose transaction bytes no copy delivers (the TMA gathers'
+// kind) -- and must latch kErrTimeout and return, leaving the context usable.
+__global__ void k_selftest_wait(uint32_t which, const unsigned long long* never_set,
+                                uint32_t* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (which == 0) {
+        uint32_t spins = 0;
+        while (*(volatile const unsigned long long*)never_set == 0) {
+            if (++spins > kSpinLimit) {
+                LEY_FAIL(err, kErrTimeout);
+                break;
+            }
+            if (spins > 32) __nanosleep(64);
+        }
+    } else {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(&bar, 16);  // 16 bytes that never arrive
+        if (!mbar_wait(&bar, 0)) LEY_FAIL(err, kErrTimeout);
+    }
+}
+
+cudaError_t launch_selftest_wait(cudaStream_t s, uint32_t which,
+                                 const unsigned long long* never_set, uint32_t* err) {
+    k_selftest_wait<<<1, 32, 0, s>>>(which, never_set, err);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- launchers
 
 static size_t tma_smem() { return (size_t)kTmaWarps * sizeof(TmaWarpBuf); }

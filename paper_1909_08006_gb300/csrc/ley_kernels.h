@@ -94,6 +94,10 @@ cudaError_t launch_batch_gather_generic(cudaStream_t s, int grid, const BatchReq
 // dst[0, bytes) = src (host), stream-ordered through kernel parameters (no
 // host buffer needs to outlive the call; capturable in a CUDA graph).
 cudaError_t launch_upload(cudaStream_t s, void* dst, const void* src, size_t bytes);
+// A bounded wait that cannot succeed (which = 0: a device word nobody sets,
+// which = 1: an mbarrier no copy completes); latches kErrTimeout in err.
+cudaError_t launch_selftest_wait(cudaStream_t s, uint32_t which,
+                                 const unsigned long long* never_set, uint32_t* err);
 // p[0, bytes) = uniform random bytes from `seed` (8-byte aligned p).
 cudaError_t launch_fill_random(cudaStream_t s, uint8_t* p, unsigned long long bytes,
                                unsigned long long seed);

@@ -22,10 +22,21 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.  The
+// bound is time (kWaitLimitNs of the global timer), because try_wait may
+// suspend the thread for an implementation-defined while per attempt.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done = 0;
-    for (uint32_t spins = 0; spins < kSpinLimit; spins++) {
+    const unsigned long long t0 = global_ns();
+    for (uint32_t spins = 0; spins < (1u << 30); spins++) {  // time bound below; count as a backstop
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -34,6 +45,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((spins & 63) == 63 && global_ns() - t0 > kWaitLimitNs) return false;
     }
     return false;
 }

@@ -258,3 +258,15 @@ def test_generator_same_on_gpu_and_cpu():
     c = datagen.skew_records(50_000, seed=9, device=DEV).cpu()
     d = datagen.skew_records(50_000, seed=9)
     assert torch.equal(c, d)
+
+
+# ------------------------------------------------- failure detection
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_gives_up_and_reports(orc, ley, which):
+    # a wait on a flag nobody sets (0) or an mbarrier no copy completes (1)
+    # must latch LEY_ETIMEOUT, clear on read, and leave the context usable
+    assert ley.ley_selftest_timeout(which) == ley.LEY_ETIMEOUT
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    rec = datagen.uniform_records(10_000, seed=12)
+    check_exact(orc, ley, rec)
