@@ -244,7 +244,7 @@ typedef struct {
     uint32_t big_bucket;          /* buckets above this many tuples are scattered again;
                                      256..2048, default 2048 (one finishing CTA's capacity) */
     uint32_t tiny_bucket;         /* sub-buckets up to this many tuples are finished by
-                                     comparison ranking; 32..256, default 32 */
+                                     comparison ranking; 32..256, default 64 */
     uint32_t finish_ctas_per_sm;  /* 0 = as many as fit (default) */
     uint32_t pass_ctas_per_sm;    /* 0 = as many as fit (default) */
 } ley_tuning;

@@ -254,7 +254,7 @@ def ley_set_tuning(tuning: dict | None) -> int:
     if tuning is None:
         return _check(_lib.ley_set_tuning(None), "ley_set_tuning")
     t = _Tuning(**{f: int(tuning.get(f, d)) for f, d in
-                   (("big_bucket", 2048), ("tiny_bucket", 32), ("finish_ctas_per_sm", 0),
+                   (("big_bucket", 2048), ("tiny_bucket", 64), ("finish_ctas_per_sm", 0),
                     ("pass_ctas_per_sm", 0))})
     return _check(_lib.ley_set_tuning(ctypes.byref(t)), "ley_set_tuning")
 

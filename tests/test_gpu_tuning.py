@@ -67,7 +67,7 @@ def test_invalid_tunings_rejected(ley):
             ley.ley_set_tuning(bad)
         assert e.value.status == ley.LEY_EINVAL
     ley.ley_set_tuning(None)
-    assert ley.ley_get_tuning() == {"big_bucket": 2048, "tiny_bucket": 32,
+    assert ley.ley_get_tuning() == {"big_bucket": 2048, "tiny_bucket": 64,
                                     "finish_ctas_per_sm": 0, "pass_ctas_per_sm": 0}
 
 
