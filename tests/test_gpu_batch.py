@@ -153,3 +153,26 @@ def test_batch_in_cuda_graph(orc, ley):
         assert ley.ley_last_device_status() == ley.LEY_OK
         for o, r in zip(outs, data):
             assert np.array_equal(o.cpu().numpy(), orc.sort_records(r.numpy()))
+
+
+def test_many_tiny_requests(orc, ley):
+    # thousands of requests of 1..5 records: as many level-0 segments, each a
+    # finishing task of its own
+    rng = np.random.default_rng(11)
+    sizes = [int(x) for x in rng.integers(1, 6, 3000)]
+    recs = [datagen.uniform_records(n, seed=7000 + i) for i, n in enumerate(sizes)]
+    for r in recs[::3]:
+        r[:, :10] = r[0, :10].clone()  # every third request: all keys equal
+    reqs = [(r.to(DEV), torch.empty(r.shape, dtype=torch.uint8, device=DEV)) for r in recs]
+    ley.ley_sort_records_batch(reqs)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    for (d_in, d_out), r in zip(reqs, recs):
+        assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(r.numpy()))
+    keys = [datagen.narrow_pairs(n, seed=i, distinct=2) for i, n in enumerate(sizes[:1000])]
+    preqs = [(k.to(DEV), v.to(DEV), torch.empty(k.shape, dtype=torch.int64, device=DEV),
+              torch.empty(v.shape, dtype=torch.int32, device=DEV)) for k, v in keys]
+    ley.ley_sort_keys_index_batch(preqs)
+    for (k, v, ko, vo), (hk, hv) in zip(preqs, keys):
+        wk, wi = orc.sort_keys_index(hk.numpy(), hv.numpy())
+        assert np.array_equal(ko.cpu().numpy().view(np.uint64), wk)
+        assert np.array_equal(vo.cpu().numpy().view(np.uint32), wi)
