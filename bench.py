@@ -233,17 +233,24 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
     launches0 = ley.ley_launch_count()
     clk.start()
     time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # an event between consecutive steps gives each step's own time too
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = evs[0], evs[-1]
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         step()
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches = ley.ley_launch_count() - launches0
     barrier(pg, dev)
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, pg, dev)
+    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    step_stats = {"median_ms": round(statistics.median(per_step), 3),
+                  "p99_ms": round(per_step[min(len(per_step) - 1,
+                                               int(0.99 * len(per_step)))], 3),
+                  "min_ms": round(per_step[0], 3), "max_ms": round(per_step[-1], 3)}
     if ley.ley_last_device_status(stream) != ley.LEY_OK:
         raise RuntimeError("device-side error in the timed region")
 
@@ -317,7 +324,8 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         "config": {"workload": workload, "records": n, "record_bytes": REC, "key_bytes": kb,
                    "resident": "HBM", "l2": "inputs larger than L2 (10 GB), no flush",
                    "parallelism": f"replicas x{world}"},
-        "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
+        "clocks": clocks, "gpu_launches": launches, "step_ms": step_stats, "e2e": e2e,
+        "roofline": roofline,
         "cpu_baseline": cpu, "kernels": kernels,
     }
 
