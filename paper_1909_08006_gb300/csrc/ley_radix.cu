@@ -1567,17 +1567,24 @@ __device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint
             uint32_t* wdst = reinterpret_cast<uint32_t*>(wreg + ph);
             // Output word q (record k = q / 25, word i) comes from window word
             // 28k + o_k + i.  Past record 0 the source never lies below the
-            // destination, and record 0 is copied within the first step, so
-            // a forward copy in steps of 32 words (all reads of a step before
-            // its writes) is safe in place.
-            for (uint32_t q0 = 0; q0 < words; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                const uint32_t k = q / kRecWords;
-                const uint32_t ok = __shfl_sync(0xffffffffu, o, k & 31);
-                uint32_t val = 0;
-                if (q < words) val = wsrc[k * (kWinBytes / 4) + ok + (q - k * kRecWords)];
+            // destination by more than the step, and record 0 is copied
+            // within the first step, so a forward copy in steps of 128 words
+            // (all reads of a step before its writes) is safe in place.
+            for (uint32_t q0 = 0; q0 < words; q0 += 128) {
+                uint32_t val[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t q = q0 + 32 * u + lane;
+                    const uint32_t k = q / kRecWords;
+                    const uint32_t ok = __shfl_sync(0xffffffffu, o, k & 31);
+                    val[u] = q < words ? wsrc[k * (kWinBytes / 4) + ok + (q - k * kRecWords)] : 0u;
+                }
                 __syncwarp();
-                if (q < words) wdst[q] = val;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t q = q0 + 32 * u + lane;
+                    if (q < words) wdst[q] = val[u];
+                }
                 __syncwarp();
             }
             fence_proxy_async_smem();
