@@ -1275,6 +1275,8 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
 #pragma unroll
         for (int k = 0; k < kFinItems; k++) {
             const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+            rd[k] = 0;
+            if (warp * (kFinItems * 32) + k * 32 >= c) continue;  // no item of the warp: skip
             const bool valid = idx < c;
             const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
             rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
@@ -1406,6 +1408,8 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
         const uint32_t idx = k * 32 + lane;
+        rd[k] = 0;
+        if (k * 32 >= (int)c) continue;  // no item of the warp: skip
         const bool valid = idx < c;
         const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
         rd[k] = (warp_rank(cnt, dk, valid, lt_mask, lane) << 8) | dk;
