@@ -1252,12 +1252,17 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
                                uint32_t c, int d0, const KeySpec& ks, uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
+    // Items per thread for this range, so that every warp holds a share:
+    // warp w owns items [w * ipt * 32, (w + 1) * ipt * 32) -- contiguous per
+    // warp, which keeps the ranks stable.
+    const uint32_t ipt = (c + kFinThreads - 1) / kFinThreads;
+    const uint32_t wbase = (uint32_t)warp * ipt * 32;
     uint4 v[kFinItems];
     uint32_t rd[kFinItems];
     const uint4 ref = FROM_GLOBAL ? gsrc[0] : B[r0];
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
-        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+        const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
         if (FROM_GLOBAL)
             v[k] = idx < c ? gsrc[idx] : ref;
         else
@@ -1274,9 +1279,9 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
 #endif
 #pragma unroll
         for (int k = 0; k < kFinItems; k++) {
-            const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+            const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
             rd[k] = 0;
-            if (warp * (kFinItems * 32) + k * 32 >= c) continue;  // no item of the warp: skip
+            if ((uint32_t)k >= ipt || wbase + k * 32 >= c) continue;  // no item of the warp: skip
             const bool valid = idx < c;
             const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
             rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
@@ -1325,7 +1330,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             // All keys equal: the input order is the answer.
 #pragma unroll
             for (int k = 0; k < kFinItems; k++) {
-                const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+                const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
                 if (idx < c) {
                     if (FROM_GLOBAL) B[r0 + idx] = v[k];
                     S.order[r0 + idx] = (uint16_t)(r0 + idx);
@@ -1338,7 +1343,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
     }
 #pragma unroll
     for (int k = 0; k < kFinItems; k++) {
-        const uint32_t idx = warp * (kFinItems * 32) + k * 32 + lane;
+        const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
         const uint32_t dk = rd[k] & 0xFFu;
         const uint32_t pos = r0 + S.sb_off[dk] + S.cnt[warp][dk] + (rd[k] >> 8);
         if (idx < c) {
