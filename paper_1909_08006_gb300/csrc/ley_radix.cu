@@ -1528,28 +1528,57 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
 
 // Record gather of one finished task: out[start + j] = in[src index of j]
 // for j < count, where the source index is sidx[j] (shared memory), or
-// src[j].w when the task's tuples are already in order (flagged).  Rounds of
-// kFinThreads records, one per thread: the record's 112-byte window is
-// bulk-copied (TMA) into B; then each warp shifts its 32 records in place
-// into 3200 contiguous output bytes and writes them as one bulk store of the
-// 16-byte aligned middle plus word stores of the ragged ends.  The staged
-// output starts at its own 16-byte phase (ph) inside the warp's window area,
-// so the aligned middle is aligned in shared memory too.  Returns false (all
-// threads alike) if a bulk copy did not land within the wait limit.
+// src[j].w when the task's tuples are already in order (flagged).
+//
+// The CTA's warps form two groups of four, each with half of B and its own
+// mbarrier, taking alternate rounds of 128 records (one per thread): a group
+// bulk-copies (TMA) its records' 112-byte windows, waits for them, shifts
+// each warp's 32 records in place into 3200 contiguous output bytes and
+// writes them as one bulk store of the 16-byte aligned middle plus word
+// stores of the ragged ends -- while the other group's copies are in flight.
+// The output is staged at its own 16-byte phase (ph) inside the warp's
+// window area, so the aligned middle is aligned in shared memory too.
+// Returns false (all threads alike) if a bulk copy did not land within the
+// wait limit.
+constexpr uint32_t kGatherHalf = kFinThreads / 2;  // records per round (128)
+
+// Barrier of one group (named barriers 1 and 2), and the same barrier
+// reducing a predicate: true only if it holds in every thread of the group.
+__device__ __forceinline__ void group_sync(int g) {
+    if (g == 0) asm volatile("bar.sync 1, %0;" ::"n"(kGatherHalf) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"n"(kGatherHalf) : "memory");
+}
+
+__device__ __forceinline__ bool group_all(int g, bool v) {
+    uint32_t r;
+    if (g == 0)
+        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                     "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(r) : "r"((uint32_t)v), "n"(kGatherHalf) : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                     "bar.red.and.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(r) : "r"((uint32_t)v), "n"(kGatherHalf) : "memory");
+    return r != 0;
+}
+
 __device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint4* src,
                                    bool flagged, ull start, uint32_t count, const Emitter<2>& e,
-                                   uint64_t* bar, uint32_t& phase, uint32_t* err) {
+                                   uint64_t* bar, uint32_t* phase, uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t* wreg = Bb + warp * (32 * kWinBytes);  // this warp's 32 windows
+    const int g = warp >> 2;                        // group: 0 or 1
+    const int gt = tid & (kGatherHalf - 1);         // thread within the group
+    uint8_t* gbuf = Bb + g * (kGatherHalf * kWinBytes);
+    uint8_t* wreg = gbuf + (warp & 3) * (32 * kWinBytes);  // this warp's 32 windows
     const uint32_t* wsrc = reinterpret_cast<const uint32_t*>(wreg);
-    for (uint32_t r0 = 0; r0 < count; r0 += kFinThreads) {
-        const uint32_t nv = min(count - r0, (uint32_t)kFinThreads);
-        const uint32_t j = r0 + tid;
-        // B's previous contents (tuples, or the last round's output, whose
-        // bulk stores have been read out) are no longer used.
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) mbar_arrive_expect_tx(bar, nv * kWinBytes);
+    bool ok_all = true;
+    // B's previous contents (the task's tuples) are no longer read.
+    fence_proxy_async_smem();
+    __syncthreads();
+    for (uint32_t r0 = (uint32_t)g * kGatherHalf; r0 < count && ok_all; r0 += 2 * kGatherHalf) {
+        const uint32_t nv = min(count - r0, kGatherHalf);
+        const uint32_t j = r0 + gt;
+        if (gt == 0) mbar_arrive_expect_tx(&bar[g], nv * kWinBytes);
         uint32_t o = 0;
         if (j < count) {
             uint32_t p = flagged ? src[j].w : sidx[j];
@@ -1559,16 +1588,15 @@ __device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint
             }
             const ull sb = (ull)p * kRec;
             o = (uint32_t)(sb & 15) >> 2;
-            tma_load_1d(Bb + tid * kWinBytes, e.in + (sb & ~15ull), kWinBytes, bar);
+            tma_load_1d(gbuf + gt * kWinBytes, e.in + (sb & ~15ull), kWinBytes, &bar[g]);
         }
-        const bool landed = mbar_wait(bar, phase);
-        if (__syncthreads_or(!landed)) {
-            if (tid == 0) LEY_FAIL(err, kErrTimeout);
-            (void)mbar_wait(bar, phase);  // a bounded chance for copies in flight
-            return false;
+        // the whole group agrees on the outcome before acting on it
+        if (!group_all(g, mbar_wait(&bar[g], phase[g]))) {
+            ok_all = false;
+            break;
         }
-        phase ^= 1u;
-        const uint32_t wr0 = (uint32_t)warp * 32;
+        phase[g] ^= 1u;
+        const uint32_t wr0 = (uint32_t)(warp & 3) * 32;
         if (wr0 < nv) {  // warp-uniform
             const uint32_t words = min(nv - wr0, 32u) * kRecWords;
             const ull g0 = (start + r0 + wr0) * kRec, g1 = g0 + 4ull * words;
@@ -1614,7 +1642,14 @@ __device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint
                 for (uint32_t q = lane; q < words; q += 32) outw[q] = wdst[q];
             }
         }
-        if (lane == 0) bulk_wait_read_0();  // B is reused by the next round or task
+        if (lane == 0) bulk_wait_read_0();  // the group's half of B is refilled next
+        fence_proxy_async_smem();
+        group_sync(g);
+    }
+    if (__syncthreads_or(!ok_all)) {
+        if (tid == 0) LEY_FAIL(err, kErrTimeout);
+        if (!ok_all) (void)mbar_wait(&bar[g], phase[g]);  // a bounded chance for late copies
+        return false;
     }
     return true;
 }
@@ -1628,13 +1663,14 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
     constexpr int TM = TaskEmit<MODE>::mode;  // how a task is emitted
-    __shared__ __align__(8) uint64_t gbar;  // TM 2: the record windows' bulk copies
-    uint32_t gphase = 0;
+    __shared__ __align__(8) uint64_t gbar[2];  // TM 2: the record windows' bulk copies
+    uint32_t gphase[2] = {0, 0};
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
     if (tid == 0) {
         S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
         if (TM == 2) {
-            mbar_init(&gbar, 1);
+            mbar_init(&gbar[0], 1);
+            mbar_init(&gbar[1], 1);
             mbar_fence_init();
         }
     }
@@ -1664,7 +1700,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
         if (!skip && (tk.flags & 1)) {  // all keys equal: input order
             if constexpr (TM == 2) {
                 if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), nullptr, src, true,
-                                        tk.start, tk.count, te, &gbar, gphase, w.err))
+                                        tk.start, tk.count, te, gbar, gphase, w.err))
                     break;
             } else {
                 for (uint32_t i = tid; i < tk.count; i += kFinThreads) te(tk.start + i, src[i]);
@@ -1711,7 +1747,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                     sidx[j] = B[o].w;
                 }
                 if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), sidx, src, false,
-                                        tk.start, tk.count, te, &gbar, gphase, w.err))
+                                        tk.start, tk.count, te, gbar, gphase, w.err))
                     break;
             } else {
                 // Coalesced write of the task's final order.
