@@ -183,6 +183,22 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool v
     return old + __popc(peers & lt_mask);
 }
 
+// The same rank without the atomic and the shuffle: every lane reads its
+// digit's count (peers read the same word); then the lowest lane of each
+// digit -- distinct digits of the warp's own row -- stores the count advanced
+// by its peers.  Faster where few warps rank at once (the finishing CTAs);
+// the atomic form is faster in the scatter pass.
+__device__ __forceinline__ uint32_t warp_rank_rw(uint32_t* cnt, uint32_t dg, bool valid,
+                                                 uint32_t lt_mask) {
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    const uint32_t peers = peers8(dg) & vmask;
+    const uint32_t old = valid ? cnt[dg] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt_mask) == 0) cnt[dg] = old + (uint32_t)__popc(peers);
+    __syncwarp();
+    return old + __popc(peers & lt_mask);
+}
+
 // ------------------------------------------------------------- extract
 
 // One tile = kPassTile consecutive records: its digit counts go to
@@ -564,6 +580,11 @@ k_hist(Work w, KeySpec ks, int L) {
         __syncthreads();
         sh_hist[tid] = 0;
         if (tid < 3) sh_d[tid] = 0;
+        // Thread 0 asks the L2 for this CTA's next tile (looked up in steps,
+        // so that no load is waited for at once).
+        const uint32_t tn = t + gridDim.x;
+        uint32_t sn = kNoPass;
+        if (tid == 0 && tn < ntiles) sn = w.seg_tile_owner[p][tn];
         __syncthreads();
         const uint32_t s = w.seg_tile_owner[p][t];
         const Seg sg = w.segs[p][s];
@@ -582,6 +603,12 @@ k_hist(Work w, KeySpec ks, int L) {
             uint32_t idx = k * kHistThreads + tid;
             v[k] = idx < m ? src[base + idx] : ref;
         }
+        Seg sgn;
+        uint32_t tbn = 0;
+        if (tid == 0 && sn < nseg) {
+            sgn = w.segs[p][sn];
+            tbn = w.seg_tile_base[p][sn];
+        }
         ull dhi = 0;
         uint32_t dlo = 0;
 #pragma unroll
@@ -592,6 +619,13 @@ k_hist(Work w, KeySpec ks, int L) {
             hist_add_vote(sh_hist, idx < m ? digit_of(v[k], sg.digit) : 256u);
         }
         warp_or_diff(dhi & ks.hi_mask, dlo & ks.lo_mask, sh_d);
+        if (tid == 0 && sn < nseg && tn >= tbn && sgn.buf <= 1 && sgn.start + sgn.count <= w.n) {
+            const ull off = (ull)(tn - tbn) * kPassTile;
+            if (off < sgn.count) {
+                const uint32_t mn = (uint32_t)min((ull)kPassTile, sgn.count - off);
+                l2_prefetch_bulk(w.tup[sgn.buf] + sgn.start + off, mn * (uint32_t)sizeof(uint4));
+            }
+        }
         __syncthreads();
         w.tile_cnt[(ull)t * kRadix + tid] = sh_hist[tid];
         if (tid == 0) flush_diff(sh_d, &w.diff[p][s]);
@@ -981,6 +1015,23 @@ __global__ void k_classify_partition(Work w) {
 //   bucket start + bucket_base[digit] + tile offset[digit] (from k_scan),
 // after ranking its tuples stably by digit and staging them in shared memory
 // so that every run is written contiguously (cache-aware scattering).
+// The tuples of tile t of level L's big list (for an L2 prefetch), or none.
+__device__ __noinline__ void pass_prefetch_target(const Work& w, int p, uint32_t nseg,
+                                                  uint32_t ntiles, uint32_t t,
+                                                  const uint4** ptr, uint32_t* bytes) {
+    *bytes = 0;
+    if (t >= ntiles) return;
+    const uint32_t s = w.seg_tile_owner[p][t];
+    if (s >= nseg) return;
+    const Seg sg = w.segs[p][s];
+    const uint32_t tb = w.seg_tile_base[p][s];
+    if (t < tb || sg.buf > 1 || sg.start + sg.count > w.n) return;
+    const ull off = (ull)(t - tb) * kPassTile;
+    if (off >= sg.count) return;
+    *ptr = w.tup[sg.buf] + sg.start + off;
+    *bytes = (uint32_t)min((ull)kPassTile, sg.count - off) * (uint32_t)sizeof(uint4);
+}
+
 __global__ void __launch_bounds__(kPassThreads, 2)
 k_pass(Work w, KeySpec ks, int L) {
     extern __shared__ uint4 stage[];                 // kPassTile tuples
@@ -1001,7 +1052,18 @@ k_pass(Work w, KeySpec ks, int L) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
     LEY_PHASE_BEGIN;
+    // Thread 0 asks the L2 for the CTA's tiles one tile ahead: while tile t
+    // is scattered, tile t + grid is being fetched and tile t + 2 grid is
+    // looked up in steps (owner, then bucket), so no lookup is waited for.
+    const uint4* pf_ptr = nullptr;
+    uint32_t pf_bytes = 0;
+    if (tid == 0) pass_prefetch_target(w, p, nseg, ntiles, blockIdx.x + gridDim.x, &pf_ptr, &pf_bytes);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (tid == 0 && pf_bytes) l2_prefetch_bulk(pf_ptr, pf_bytes);
+        pf_bytes = 0;
+        const uint32_t tn = t + 2 * gridDim.x;
+        uint32_t sn = kNoPass;
+        if (tid == 0 && tn < ntiles) sn = w.seg_tile_owner[p][tn];
         const uint32_t s = w.seg_tile_owner[p][t];
         const uint32_t e = s < nseg ? w.seg_pass[p][s] : kNoPass;
         if (e == kNoPass) continue;  // bucket not scattered at this level
@@ -1036,6 +1098,13 @@ k_pass(Work w, KeySpec ks, int L) {
             v[k] = idx < m ? src[base + idx] : make_uint4(0, 0, 0, 0);
         }
         __syncthreads();  // counters zeroed
+#ifdef LEY_PHASE_TIMING
+        if (tid == 0) {  // thread 0 waits for its own loads
+            volatile uint32_t sink = v[0].x ^ v[kPassItems - 1].w;
+            (void)sink;
+        }
+#endif
+        LEY_PHASE(6);
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
             const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
@@ -1043,8 +1112,15 @@ k_pass(Work w, KeySpec ks, int L) {
             const uint32_t dk = valid ? digit_of(v[k], d) : 0u;
             rd[k] = (warp_rank(wcnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
         }
+        LEY_PHASE(5);
         __syncthreads();
         LEY_PHASE(1);
+        Seg sgn;
+        uint32_t tbn = 0;
+        if (tid == 0 && sn < nseg) {
+            sgn = w.segs[p][sn];
+            tbn = w.seg_tile_base[p][sn];
+        }
         uint32_t tile_cnt = 0, incl = 0;
         if (tid < kRadix) {
             // Thread `tid` owns digit tid: exclusive offsets over warps, then
@@ -1087,6 +1163,13 @@ k_pass(Work w, KeySpec ks, int L) {
         }
         __syncthreads();
         LEY_PHASE(3);
+        if (tid == 0 && sn < nseg && tn >= tbn && sgn.buf <= 1 && sgn.start + sgn.count <= w.n) {
+            const ull off = (ull)(tn - tbn) * kPassTile;
+            if (off < sgn.count) {
+                pf_ptr = w.tup[sgn.buf] + sgn.start + off;
+                pf_bytes = (uint32_t)min((ull)kPassTile, sgn.count - off) * (uint32_t)sizeof(uint4);
+            }
+        }
         // Write each digit's run contiguously to its bucket.
         const ull seg_end = sg.start + sg.count;
         for (uint32_t i = tid; i < m; i += kPassThreads) {
@@ -1284,7 +1367,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             if ((uint32_t)k >= ipt || wbase + k * 32 >= c) continue;  // no item of the warp: skip
             const bool valid = idx < c;
             const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
-            rd[k] = (warp_rank(S.cnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
+            rd[k] = (warp_rank_rw(S.cnt[warp], dk, valid, lt_mask) << 8) | dk;
         }
         __syncthreads();
         {
@@ -1417,7 +1500,7 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
         if (k * 32 >= (int)c) continue;  // no item of the warp: skip
         const bool valid = idx < c;
         const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
-        rd[k] = (warp_rank(cnt, dk, valid, lt_mask, lane) << 8) | dk;
+        rd[k] = (warp_rank_rw(cnt, dk, valid, lt_mask) << 8) | dk;
     }
     __syncwarp();
     // Exclusive scan of the 256 counters: lane l owns bins 8l..8l+7.
