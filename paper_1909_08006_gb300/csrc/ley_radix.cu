@@ -1613,56 +1613,27 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
 // for j < count, where the source index is sidx[j] (shared memory), or
 // src[j].w when the task's tuples are already in order (flagged).
 //
-// The CTA's warps form two groups of four, each with half of B and its own
-// mbarrier, taking alternate rounds of 128 records (one per thread): a group
-// bulk-copies (TMA) its records' 112-byte windows, waits for them, shifts
-// each warp's 32 records in place into 3200 contiguous output bytes and
-// writes them as one bulk store of the 16-byte aligned middle plus word
-// stores of the ragged ends -- while the other group's copies are in flight.
-// The output is staged at its own 16-byte phase (ph) inside the warp's
-// window area, so the aligned middle is aligned in shared memory too.
-// Returns false (all threads alike) if a bulk copy did not land within the
-// wait limit.
-constexpr uint32_t kGatherHalf = kFinThreads / 2;  // records per round (128)
-
-// Barrier of one group (named barriers 1 and 2), and the same barrier
-// reducing a predicate: true only if it holds in every thread of the group.
-__device__ __forceinline__ void group_sync(int g) {
-    if (g == 0) asm volatile("bar.sync 1, %0;" ::"n"(kGatherHalf) : "memory");
-    else asm volatile("bar.sync 2, %0;" ::"n"(kGatherHalf) : "memory");
-}
-
-__device__ __forceinline__ bool group_all(int g, bool v) {
-    uint32_t r;
-    if (g == 0)
-        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-                     "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(r) : "r"((uint32_t)v), "n"(kGatherHalf) : "memory");
-    else
-        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-                     "bar.red.and.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(r) : "r"((uint32_t)v), "n"(kGatherHalf) : "memory");
-    return r != 0;
-}
-
-__device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint4* src,
+// Each warp owns 32 of B's 112-byte windows and takes rounds of 32 records
+// (round r of the task goes to warp r % 8), independently of the other
+// warps.  Its lanes copy the records' 16-byte aligned windows as 16-byte
+// asynchronous copies (cp.async: many small copies in flight at once), wait
+// for their own, shift the 32 records in place into 3200 contiguous output
+// bytes, and write them as one bulk store of the 16-byte aligned middle plus
+// word stores of the ragged ends.  The output is staged at its own 16-byte
+// phase (ph) inside the warp's windows, so the aligned middle is aligned in
+// shared memory too.
+__device__ void fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint4* src,
                                    bool flagged, ull start, uint32_t count, const Emitter<2>& e,
-                                   uint64_t* bar, uint32_t* phase, uint32_t* err) {
+                                   uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = warp >> 2;                        // group: 0 or 1
-    const int gt = tid & (kGatherHalf - 1);         // thread within the group
-    uint8_t* gbuf = Bb + g * (kGatherHalf * kWinBytes);
-    uint8_t* wreg = gbuf + (warp & 3) * (32 * kWinBytes);  // this warp's 32 windows
+    uint8_t* wreg = Bb + warp * (32 * kWinBytes);  // this warp's 32 windows
     const uint32_t* wsrc = reinterpret_cast<const uint32_t*>(wreg);
-    bool ok_all = true;
-    // B's previous contents (the task's tuples) are no longer read.
-    fence_proxy_async_smem();
-    __syncthreads();
-    for (uint32_t r0 = (uint32_t)g * kGatherHalf; r0 < count && ok_all; r0 += 2 * kGatherHalf) {
-        const uint32_t nv = min(count - r0, kGatherHalf);
-        const uint32_t j = r0 + gt;
-        if (gt == 0) mbar_arrive_expect_tx(&bar[g], nv * kWinBytes);
+    __syncthreads();  // B's previous contents (the task's tuples) are no longer read
+    for (uint32_t r0 = (uint32_t)warp * 32; r0 < count; r0 += kFinThreads) {
+        const uint32_t nv = min(count - r0, 32u);
+        const uint32_t j = r0 + lane;
         uint32_t o = 0;
+        ull wsb = 0;  // this lane's record's aligned window (byte offset in the input)
         if (j < count) {
             uint32_t p = flagged ? src[j].w : sidx[j];
             if (p >= e.n_in) {  // never for a valid task list; keeps reads in bounds
@@ -1671,70 +1642,70 @@ __device__ bool fin_gather_records(uint8_t* Bb, const uint32_t* sidx, const uint
             }
             const ull sb = (ull)p * kRec;
             o = (uint32_t)(sb & 15) >> 2;
-            tma_load_1d(gbuf + gt * kWinBytes, e.in + (sb & ~15ull), kWinBytes, &bar[g]);
+            wsb = sb & ~15ull;
         }
-        // the whole group agrees on the outcome before acting on it
-        if (!group_all(g, mbar_wait(&bar[g], phase[g]))) {
-            ok_all = false;
-            break;
+        // The 32 windows as 224 16-byte pieces: piece c is part c % 7 of
+        // record c / 7; lane l copies pieces l, l + 32, ..., l + 192.
+#pragma unroll
+        for (int u = 0; u < 7; u++) {
+            const uint32_t c = (uint32_t)lane + 32u * u;
+            const uint32_t k = c / 7u, part = c - 7u * k;
+            const ull kb = __shfl_sync(0xffffffffu, wsb, (int)k);
+            if (k < nv)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             ::"r"(smem_addr(wreg + k * kWinBytes + part * 16)),
+                             "l"(e.in + kb + part * 16)
+                             : "memory");
         }
-        phase[g] ^= 1u;
-        const uint32_t wr0 = (uint32_t)(warp & 3) * 32;
-        if (wr0 < nv) {  // warp-uniform
-            const uint32_t words = min(nv - wr0, 32u) * kRecWords;
-            const ull g0 = (start + r0 + wr0) * kRec, g1 = g0 + 4ull * words;
-            const uint32_t ph = (uint32_t)(g0 & 15);  // 0, 4, 8 or 12
-            uint32_t* wdst = reinterpret_cast<uint32_t*>(wreg + ph);
-            // Output word q (record k = q / 25, word i) comes from window word
-            // 28k + o_k + i.  Past record 0 the source never lies below the
-            // destination by more than the step, and record 0 is copied
-            // within the first step, so a forward copy in steps of 128 words
-            // (all reads of a step before its writes) is safe in place.
-            for (uint32_t q0 = 0; q0 < words; q0 += 128) {
-                uint32_t val[4];
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncwarp();  // every lane's pieces have landed
+        const uint32_t words = nv * kRecWords;
+        const ull g0 = (start + r0) * kRec, g1 = g0 + 4ull * words;
+        const uint32_t ph = (uint32_t)(g0 & 15);  // 0, 4, 8 or 12
+        uint32_t* wdst = reinterpret_cast<uint32_t*>(wreg + ph);
+        // Output word q (record k = q / 25, word i) comes from window word
+        // 28k + o_k + i.  Past record 0 the source never lies below the
+        // destination by more than the step, and record 0 is copied within
+        // the first step, so a forward copy in steps of 128 words (all reads
+        // of a step before its writes) is safe in place.
+        for (uint32_t q0 = 0; q0 < words; q0 += 128) {
+            uint32_t val[4];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t q = q0 + 32 * u + lane;
-                    const uint32_t k = q / kRecWords;
-                    const uint32_t ok = __shfl_sync(0xffffffffu, o, k & 31);
-                    val[u] = q < words ? wsrc[k * (kWinBytes / 4) + ok + (q - k * kRecWords)] : 0u;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t q = q0 + 32 * u + lane;
-                    if (q < words) wdst[q] = val[u];
-                }
-                __syncwarp();
+            for (int u = 0; u < 4; u++) {
+                const uint32_t q = q0 + 32 * u + lane;
+                const uint32_t k = q / kRecWords;
+                const uint32_t ok = __shfl_sync(0xffffffffu, o, k & 31);
+                val[u] = q < words ? wsrc[k * (kWinBytes / 4) + ok + (q - k * kRecWords)] : 0u;
             }
-            fence_proxy_async_smem();
             __syncwarp();
-            const ull a0 = (g0 + 15) & ~15ull, a1 = g1 & ~15ull;
-            uint32_t* outw = reinterpret_cast<uint32_t*>(e.out + g0);
-            if (a1 > a0) {
-                const uint32_t head = (uint32_t)(a0 - g0) >> 2;
-                const uint32_t tail0 = (uint32_t)(a1 - g0) >> 2, tail = words - tail0;
-                if ((uint32_t)lane < head) outw[lane] = wdst[lane];
-                if (lane >= 8 && (uint32_t)lane - 8 < tail) outw[tail0 + lane - 8] = wdst[tail0 + lane - 8];
-                if (lane == 0) {
-                    tma_store_1d(e.out + a0, reinterpret_cast<uint8_t*>(wdst) + (a0 - g0),
-                                 (uint32_t)(a1 - a0));
-                    bulk_commit();
-                }
-            } else {
-                for (uint32_t q = lane; q < words; q += 32) outw[q] = wdst[q];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t q = q0 + 32 * u + lane;
+                if (q < words) wdst[q] = val[u];
             }
+            __syncwarp();
         }
-        if (lane == 0) bulk_wait_read_0();  // the group's half of B is refilled next
-        fence_proxy_async_smem();
-        group_sync(g);
+        fence_proxy_async_smem();  // the shifted words are read by the bulk store
+        __syncwarp();
+        const ull a0 = (g0 + 15) & ~15ull, a1 = g1 & ~15ull;
+        uint32_t* outw = reinterpret_cast<uint32_t*>(e.out + g0);
+        if (a1 > a0) {
+            const uint32_t head = (uint32_t)(a0 - g0) >> 2;
+            const uint32_t tail0 = (uint32_t)(a1 - g0) >> 2, tail = words - tail0;
+            if ((uint32_t)lane < head) outw[lane] = wdst[lane];
+            if (lane >= 8 && (uint32_t)lane - 8 < tail) outw[tail0 + lane - 8] = wdst[tail0 + lane - 8];
+            if (lane == 0) {
+                tma_store_1d(e.out + a0, reinterpret_cast<uint8_t*>(wdst) + (a0 - g0),
+                             (uint32_t)(a1 - a0));
+                bulk_commit();
+                bulk_wait_read_0();  // the windows are refilled next round
+            }
+        } else {
+            for (uint32_t q = lane; q < words; q += 32) outw[q] = wdst[q];
+        }
+        __syncwarp();
     }
-    if (__syncthreads_or(!ok_all)) {
-        if (tid == 0) LEY_FAIL(err, kErrTimeout);
-        if (!ok_all) (void)mbar_wait(&bar[g], phase[g]);  // a bounded chance for late copies
-        return false;
-    }
-    return true;
+    __syncthreads();  // B is reused by the next task
 }
 
 template <int MODE>
@@ -1746,17 +1717,8 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
     constexpr int TM = TaskEmit<MODE>::mode;  // how a task is emitted
-    __shared__ __align__(8) uint64_t gbar[2];  // TM 2: the record windows' bulk copies
-    uint32_t gphase[2] = {0, 0};
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
-    if (tid == 0) {
-        S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
-        if (TM == 2) {
-            mbar_init(&gbar[0], 1);
-            mbar_init(&gbar[1], 1);
-            mbar_fence_init();
-        }
-    }
+    if (tid == 0) S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
     LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
@@ -1782,9 +1744,8 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
         const typename TaskEmit<MODE>::type te = TaskEmit<MODE>::get(emit, tk.start);
         if (!skip && (tk.flags & 1)) {  // all keys equal: input order
             if constexpr (TM == 2) {
-                if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), nullptr, src, true,
-                                        tk.start, tk.count, te, gbar, gphase, w.err))
-                    break;
+                fin_gather_records(reinterpret_cast<uint8_t*>(B), nullptr, src, true, tk.start,
+                                   tk.count, te, w.err);
             } else {
                 for (uint32_t i = tid; i < tk.count; i += kFinThreads) te(tk.start + i, src[i]);
             }
@@ -1829,9 +1790,8 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                     }
                     sidx[j] = B[o].w;
                 }
-                if (!fin_gather_records(reinterpret_cast<uint8_t*>(B), sidx, src, false,
-                                        tk.start, tk.count, te, gbar, gphase, w.err))
-                    break;
+                fin_gather_records(reinterpret_cast<uint8_t*>(B), sidx, src, false, tk.start,
+                                   tk.count, te, w.err);
             } else {
                 // Coalesced write of the task's final order.
                 for (uint32_t j = tid; j < tk.count; j += kFinThreads) {
