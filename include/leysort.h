@@ -304,8 +304,9 @@ ley_status ley_sort_records_noalloc(const void* in, void* out, uint64_t n, uint3
  * Failure-detection self-test: launches a kernel whose bounded wait cannot
  * succeed -- which = 0: a device word that nothing writes (the kind of wait
  * of the scan's look-back); which = 1: an mbarrier whose bytes no copy
- * delivers (the kind of wait of the TMA gathers) -- waits for it and returns
- * the device status it latched, which is LEY_ETIMEOUT when detection works.
+ * delivers (the kind of wait of the standalone TMA gather of the host
+ * modes) -- waits for it and returns the device status it latched, which is
+ * LEY_ETIMEOUT when detection works.
  * The status word is cleared on return and the context stays usable.  Takes
  * about as long as one wait's limit (a second or less).
  */
