@@ -11,7 +11,10 @@ gather.
 
 Prints one JSON line.  ``value`` is device-timed (CUDA events on the sorting
 stream); ``e2e`` is the same metric through the C ABI with pinned host
-buffers (host->device and device->host copies inside the timed region);
+buffers (host->device and device->host copies inside the timed region): host
+to host sorts queued back to back on two streams (ley_sort_records_async), so
+one step's copy out overlaps the next step's copy in, with the latency of one
+blocking call beside it (``single_call_ms``);
 ``roofline`` is the dominant kernel's algorithmic bytes over its measured
 launch time against the measured HBM copy bandwidth; ``cpu_baseline`` is the
 CPU oracle timed on a bounded sample on this host.  With N > 1 (torchrun)
@@ -197,6 +200,7 @@ def run_ours(args, world, rank, local, pg):
 
 
 def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
+    import numpy as np
     import torch
     import datagen
     import paper_1909_08006_gb300 as ley
@@ -289,21 +293,55 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
+        # Host buffers from cuMemHostAlloc (exact size); the input is the same
+        # records, copied out of HBM once.
         del d_out
-        h_in = d_in.cpu().pin_memory()
+        h_in = host_alloc(n * REC)
+        torch.from_numpy(h_in).view(n, REC).copy_(d_in)
         del d_in
         torch.cuda.empty_cache()
-        h_out = torch.empty_like(h_in).pin_memory()
-        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
+        h_outs = [host_alloc(n * REC) for _ in range(2)]
+        addr_in = h_in.ctypes.data
+        addr_out = [a.ctypes.data for a in h_outs]
+        streams = [stream, torch.cuda.Stream(dev)]
+        # warm-up: one sort queued on each stream (each gets its own scratch)
+        for k in range(2):
+            ley.ley_sort_records_async(addr_in, addr_out[k], n=n, rec_bytes=REC, key_bytes=kb,
+                                       stream=streams[k])
+        for st in streams:
+            st.synchronize()
+        # one blocking call: the latency of a single sort, host to host
+        t0 = time.perf_counter()
+        ley.ley_sort_records(addr_in, addr_out[0], n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
+        lat = time.perf_counter() - t0
+        # The timed steps, queued alternately on the two streams: every step
+        # copies its input in and its sorted records out, and one step's copy
+        # out overlaps the next one's copy in on the link's two directions.
         barrier(pg, dev)
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
+        for k in range(args.e2e_steps):
+            ley.ley_sort_records_async(addr_in, addr_out[k % 2], n=n, rec_bytes=REC,
+                                       key_bytes=kb, stream=streams[k % 2])
+        for st in streams:
+            st.synchronize()
         dt = (time.perf_counter() - t0) / args.e2e_steps
+        if ley.ley_last_device_status(stream) != ley.LEY_OK:
+            raise RuntimeError("device-side error in the end-to-end steps")
+        if args.e2e_steps > 1 and not np.array_equal(h_outs[0], h_outs[1]):
+            raise RuntimeError("end-to-end outputs of the two streams differ")
         dt = max_over_ranks(dt, pg, dev)
+        for a in [h_in] + h_outs:
+            host_free(a)
+        # the link measured now, in this process: with both directions busy
+        # a step cannot take less than n * REC / duplex_each
+        lp = link_peaks(dev)
+        floor_ms = n * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
         e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
                "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": n * REC,
-               "d2h_bytes_per_step": n * REC}
+               "d2h_bytes_per_step": n * REC, "streams": 2,
+               "single_call_ms": round(lat * 1e3, 2), "link": lp,
+               "duplex_floor_ms": round(floor_ms, 2),
+               "floor_frac": round(floor_ms / (dt * 1e3), 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -734,7 +772,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=100_000_000)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)

@@ -85,6 +85,24 @@ ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_
                             uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream);
 
 /*
+ * As ley_sort_records, but a sort of pinned host buffers in the partially
+ * in-memory mode (Section 4.1) is only queued on `stream`: the call returns
+ * once the copy in, the sort and the copy out are enqueued, and the caller
+ * synchronises `stream` before reading `out`, changing `in` or freeing
+ * either.  Calls on different streams run concurrently, so one sort's copy
+ * out overlaps the next one's copy in on the two directions of the host
+ * link.  Each call in flight holds its own device scratch (n * rec_bytes plus
+ * the workspace, within mem_budget).  Where the input does not fit the
+ * partial mode the external sort runs and the call blocks, as
+ * ley_sort_records does.  Device buffers: identical to ley_sort_records.
+ * Errors found after the call returned surface at the stream's
+ * synchronisation (CUDA errors) or in ley_last_device_status (device-side
+ * status).
+ */
+ley_status ley_sort_records_async(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                                  uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream);
+
+/*
  * Sort (key, payload) pairs: keys_in[i] as unsigned 64-bit, ties by input
  * position i; idx_in[i] travels with its key.  This is the key-pointer sort of
  * Section 3.2 (and the prefix/pointer pairs of Section 2.1) without a record

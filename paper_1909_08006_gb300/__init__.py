@@ -19,7 +19,8 @@ from . import build as _build
 
 __all__ = [
     "LeyError", "LEY_OK", "LEY_EINVAL", "LEY_ENOMEM", "LEY_EUNSUPPORTED", "LEY_ECUDA",
-    "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
+    "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_records_async", "ley_sort_keys_index",
+    "ley_partition_records",
     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
     "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS", "ley_merge_records",
@@ -86,6 +87,8 @@ def _load() -> ctypes.CDLL:
     vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
     lib.ley_sort_records.argtypes = [vp, vp, u64, u32, u32, u64, vp]
     lib.ley_sort_records.restype = ctypes.c_int
+    lib.ley_sort_records_async.argtypes = [vp, vp, u64, u32, u32, u64, vp]
+    lib.ley_sort_records_async.restype = ctypes.c_int
     lib.ley_sort_keys_index.argtypes = [vp, vp, vp, vp, u64, u64, vp]
     lib.ley_sort_keys_index.restype = ctypes.c_int
     lib.ley_partition_records.argtypes = [vp, u64, u32, u32, u32, vp, vp, vp]
@@ -195,6 +198,20 @@ def ley_sort_records(inp, out, n: int | None = None, rec_bytes: int | None = Non
     st = _lib.ley_sort_records(_addr(inp), _addr(out), n, rec_bytes, key_bytes, mem_budget,
                                _stream(stream, inp, out))
     return _check(st, "ley_sort_records")
+
+
+def ley_sort_records_async(inp, out, n: int | None = None, rec_bytes: int | None = None,
+                           key_bytes: int = 10, mem_budget: int = 0, stream=None) -> int:
+    """As ley_sort_records, but a sort of pinned host buffers is only queued
+    on ``stream`` (synchronise it before reading ``out``); see
+    ``ley_sort_records_async`` in include/leysort.h."""
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
+    st = _lib.ley_sort_records_async(_addr(inp), _addr(out), n, rec_bytes, key_bytes,
+                                     mem_budget, _stream(stream, inp, out))
+    return _check(st, "ley_sort_records_async")
 
 
 def ley_sort_records_batch(requests, rec_bytes: int = 100, key_bytes: int = 10,

@@ -92,6 +92,15 @@ static DevState* dev_state() {
         uint64_t keep = ~0ull;
         if (cudaMemPoolSetAttribute(s.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
             return nullptr;
+        // Memory freed on one stream is not handed to an allocation on another
+        // by making the second stream wait for the first (the default): calls
+        // on different streams (queued host-memory sorts, the server's slots)
+        // would otherwise run one after the other.  Reuse of frees that have
+        // already completed, and on the same stream, stays allowed.
+        int no = 0;
+        if (cudaMemPoolSetAttribute(s.pool, cudaMemPoolReuseAllowInternalDependencies, &no) !=
+            cudaSuccess)
+            return nullptr;
         (void)blocks_per_sm(KK_PASS);  // occupancy tables and smem attributes
         set_l2_fetch_granularity();
         s.init = true;
@@ -575,6 +584,10 @@ struct HostPipe {
     cudaStream_t gth = nullptr;  // record gathers into the copy-out staging buffers
     std::vector<cudaEvent_t> evs;
     bool ok = true;
+    // Whether the destructor waits for the side streams.  Without it the
+    // streams and events are released once their work completes (CUDA defers
+    // their destruction), and the caller's stream orders everything after.
+    bool drain = true;
     explicit HostPipe(cudaStream_t st) {
         // the gathers feed the writer: their kernels go first when SMs free up
         int lo_prio = 0, hi_prio = 0;
@@ -631,9 +644,11 @@ struct HostPipe {
         marks.push_back({w, e});
     }
     ~HostPipe() {
-        if (h2d) cudaStreamSynchronize(h2d);
-        if (d2h) cudaStreamSynchronize(d2h);
-        if (gth) cudaStreamSynchronize(gth);
+        if (drain || !marks.empty()) {
+            if (h2d) cudaStreamSynchronize(h2d);
+            if (d2h) cudaStreamSynchronize(d2h);
+            if (gth) cudaStreamSynchronize(gth);
+        }
         if (!marks.empty()) {
             cudaEventSynchronize(marks.back().e);
             for (auto& m : marks) {
@@ -710,7 +725,11 @@ static ull staging_records(ull n, uint32_t rec, ull budget) {
 // on the device, extraction overlapped with the copy in, and the sorted
 // records streamed back through two staging buffers.  Blocks.  Returns
 // LEY_ENOMEM without touching anything if it does not fit the budget.
-static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t st) {
+// With block false the whole pipeline is only enqueued: every side stream
+// joins `st` before the scratch is freed on it, so work queued on `st` later
+// (or a synchronisation of `st`) comes after the sorted records are in out.
+static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t st,
+                                   bool block = true) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     const ull bytes = a.n * a.rec;
@@ -731,6 +750,7 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
     {
         HostPipe hp(st);
         if (!hp.ok) s = LEY_ECUDA;
+        hp.drain = block;
         SortArgs d = a;
         d.in = reinterpret_cast<const uint8_t*>(din);
         Work w = make_work(ws, L, a.n, ds->err);
@@ -761,8 +781,10 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         hp.mark(st, "gathered");
         hp.mark(hp.d2h, "out end");
         if (!hp.order(hp.d2h, st) && s == LEY_OK) s = LEY_ECUDA;
+        if (!hp.order(hp.gth, st) && s == LEY_OK) s = LEY_ECUDA;
+        if (!hp.order(hp.h2d, st) && s == LEY_OK) s = LEY_ECUDA;
         cudaFreeAsync(dmem, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
+        if (block && cudaStreamSynchronize(st) != cudaSuccess && s == LEY_OK) s = LEY_ECUDA;
     }
     return s;
 }
@@ -1161,8 +1183,9 @@ static int external_design() {
 }
 
 // Host-memory sort: partially in-memory when it fits the budget, else external.
-static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st) {
-    ley_status s = run_host_partial(a, budget, st);
+static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st,
+                                bool block = true) {
+    ley_status s = run_host_partial(a, budget, st, block);
     if (s != LEY_ENOMEM || !budget) return s;
     if (external_design() == 1) {
         s = run_host_keys_only(a, budget, st);
@@ -1239,8 +1262,9 @@ using namespace ley;
 
 extern "C" {
 
-ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
-                            uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
+static ley_status sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                               uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream,
+                               bool block) {
     if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 4 ||
         rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
@@ -1261,8 +1285,18 @@ ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_
         if (!aligned16(in) || !aligned16(out)) return LEY_EINVAL;
         return run_device_sort(a, mem_budget, st);
     }
-    if (ki == MK_HOST_PINNED && ko == MK_HOST_PINNED) return run_host_sort(a, mem_budget, st);
+    if (ki == MK_HOST_PINNED && ko == MK_HOST_PINNED) return run_host_sort(a, mem_budget, st, block);
     return LEY_EINVAL;
+}
+
+ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                            uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
+    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, true);
+}
+
+ley_status ley_sort_records_async(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
+                                  uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
+    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, false);
 }
 
 ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,

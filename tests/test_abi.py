@@ -74,6 +74,14 @@ def test_argument_checks_before_any_gpu_work(ley):
     with pytest.raises(ley.LeyError) as e:
         ley.ley_sort_records(0, 0, n=5, rec_bytes=100, key_bytes=10)
     assert e.value.status == ley.LEY_EINVAL
+    # the queued variant checks its arguments the same way
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_sort_records_async(0, 0, n=10, rec_bytes=100, key_bytes=0)
+    assert e.value.status == ley.LEY_EUNSUPPORTED
+    assert ley.ley_sort_records_async(0, 0, n=0, rec_bytes=100, key_bytes=10) == ley.LEY_OK
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_sort_records_async(0, 0, n=5, rec_bytes=100, key_bytes=10)
+    assert e.value.status == ley.LEY_EINVAL
 
 
 def test_launch_counter_and_profiler_are_host_state(ley):

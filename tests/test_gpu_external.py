@@ -64,6 +64,46 @@ def test_partial_sort_exact(orc, ley, n):
     assert np.array_equal(got, orc.sort_records(rec.numpy()))
 
 
+def test_queued_partial_sorts_on_two_streams_exact(orc, ley):
+    """ley_sort_records_async: host-memory sorts queued on two streams with no
+    synchronisation between the calls, so copies of different sorts overlap;
+    each output equals the oracle's."""
+    gens = [lambda n, s: datagen.skew_records(n, seed=s), lambda n, s: datagen.uniform_records(n, seed=s)]
+    sizes = [1, 4097, 250_000, 1_000_000, 33_333, 600_001]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    jobs = []
+    for i, n in enumerate(sizes):
+        rec = gens[i % 2](n, 40 + i).pin_memory()
+        out = torch.zeros_like(rec).pin_memory()
+        ley.ley_sort_records_async(rec, out, key_bytes=10, stream=streams[i % 2])
+        jobs.append((rec, out))
+    for st in streams:
+        st.synchronize()
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    for rec, out in jobs:
+        assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy()))
+
+
+def test_queued_sort_falls_back_to_blocking_external(orc, ley):
+    # the budget is below the partial mode's need: the external sort runs and
+    # the call returns with the records in place
+    rec = datagen.skew_records(600_001, seed=8).pin_memory()
+    out = torch.zeros_like(rec).pin_memory()
+    ley.ley_sort_records_async(rec, out, key_bytes=10, mem_budget=50 << 20)
+    assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy()))
+
+
+def test_queued_sort_of_device_buffers_is_the_sort(orc, ley):
+    rec = datagen.uniform_records(300_000, seed=9)
+    d_in = rec.to("cuda:0")
+    a, b = torch.empty_like(d_in), torch.empty_like(d_in)
+    ley.ley_sort_records_async(d_in, a, key_bytes=10)
+    ley.ley_sort_records(d_in, b, key_bytes=10)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert np.array_equal(a.cpu().numpy(), orc.sort_records(rec.numpy()))
+
+
 def test_release_cache_between_sorts(orc, ley):
     # the device pool and the pinned run scratch are returned, then rebuilt
     rec = datagen.uniform_records(120_000, seed=21)
