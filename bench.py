@@ -310,6 +310,7 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
                                        stream=streams[k])
         for st in streams:
             st.synchronize()
+        lp0 = link_peaks(dev)  # the link before the steps (and again after them)
         # one blocking call: the latency of a single sort, host to host
         t0 = time.perf_counter()
         ley.ley_sort_records(addr_in, addr_out[0], n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
@@ -332,14 +333,18 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         dt = max_over_ranks(dt, pg, dev)
         for a in [h_in] + h_outs:
             host_free(a)
-        # the link measured now, in this process: with both directions busy
-        # a step cannot take less than n * REC / duplex_each
-        lp = link_peaks(dev)
+        # The link measured in this process before and after the steps (the
+        # better of the two readings): with both directions busy a step cannot
+        # take less than n * REC / duplex_each.  Rates on the shared hosts
+        # drift between and within processes.
+        lp1 = link_peaks(dev)
+        lp = {k: max(lp0[k], lp1[k]) for k in lp0}
         floor_ms = n * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
         e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
                "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": n * REC,
                "d2h_bytes_per_step": n * REC, "streams": 2,
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
+               "link_before": lp0, "link_after": lp1,
                "duplex_floor_ms": round(floor_ms, 2),
                "floor_frac": round(floor_ms / (dt * 1e3), 4)}
 
