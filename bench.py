@@ -300,12 +300,13 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         torch.from_numpy(h_in).view(n, REC).copy_(d_in)
         del d_in
         torch.cuda.empty_cache()
-        h_outs = [host_alloc(n * REC) for _ in range(2)]
+        ns = max(1, args.e2e_streams)
+        h_outs = [host_alloc(n * REC) for _ in range(ns)]
         addr_in = h_in.ctypes.data
         addr_out = [a.ctypes.data for a in h_outs]
-        streams = [stream, torch.cuda.Stream(dev)]
+        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(ns - 1)]
         # warm-up: one sort queued on each stream (each gets its own scratch)
-        for k in range(2):
+        for k in range(ns):
             ley.ley_sort_records_async(addr_in, addr_out[k], n=n, rec_bytes=REC, key_bytes=kb,
                                        stream=streams[k])
         for st in streams:
@@ -315,21 +316,22 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         t0 = time.perf_counter()
         ley.ley_sort_records(addr_in, addr_out[0], n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
         lat = time.perf_counter() - t0
-        # The timed steps, queued alternately on the two streams: every step
-        # copies its input in and its sorted records out, and one step's copy
-        # out overlaps the next one's copy in on the link's two directions.
+        # The timed steps, queued in turn on the streams: every step copies its
+        # input in and its sorted records out, and one step's copy out
+        # overlaps the next ones' copies in on the link's two directions.
         barrier(pg, dev)
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            ley.ley_sort_records_async(addr_in, addr_out[k % 2], n=n, rec_bytes=REC,
-                                       key_bytes=kb, stream=streams[k % 2])
+            ley.ley_sort_records_async(addr_in, addr_out[k % ns], n=n, rec_bytes=REC,
+                                       key_bytes=kb, stream=streams[k % ns])
         for st in streams:
             st.synchronize()
         dt = (time.perf_counter() - t0) / args.e2e_steps
         if ley.ley_last_device_status(stream) != ley.LEY_OK:
             raise RuntimeError("device-side error in the end-to-end steps")
-        if args.e2e_steps > 1 and not np.array_equal(h_outs[0], h_outs[1]):
-            raise RuntimeError("end-to-end outputs of the two streams differ")
+        for a in h_outs[1:min(ns, args.e2e_steps)]:
+            if not np.array_equal(h_outs[0], a):
+                raise RuntimeError("end-to-end outputs of the streams differ")
         dt = max_over_ranks(dt, pg, dev)
         for a in [h_in] + h_outs:
             host_free(a)
@@ -342,7 +344,7 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         floor_ms = n * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
         e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
                "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": n * REC,
-               "d2h_bytes_per_step": n * REC, "streams": 2,
+               "d2h_bytes_per_step": n * REC, "streams": ns,
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
                "link_before": lp0, "link_after": lp1,
                "duplex_floor_ms": round(floor_ms, 2),
@@ -778,6 +780,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=100_000_000)
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-streams", type=int, default=2,
+                    help="streams the end-to-end steps are queued on in turn")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20_000_000)
