@@ -59,3 +59,23 @@ def test_reference_arm_runs_on_rank_zero_only():
     json.dumps(out)
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_line_keeps_the_contract():
+    # the keys the reference arm's JSON line must carry, with the e2e object
+    # and the cpu_baseline describing the same run
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(ref_sample=20_000, warmup=3, steps=2, n=100_000_000)
+    out = bench.run_reference(args, world=1, rank=0, pg=None)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e", "impl"):
+        assert k in out, k
+    assert out["unit"] == "GB/s" and out["higher_is_better"] is True
+    assert out["warmup"] >= 3 and out["steps"] == 2
+    assert out["cpu_baseline"]["value"] == out["value"] and out["cpu_baseline"]["cores"] >= 1
+    assert out["e2e"]["value"] == out["value"] and out["e2e"]["unit"] == out["unit"]
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
+    assert out["config"]["workload"].startswith("uniform_")
