@@ -294,27 +294,28 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
     e2e = None
     if not args.no_e2e:
         # Host buffers from cuMemHostAlloc (exact size); the input is the same
-        # records, copied out of HBM once.
+        # records, copied out of HBM once.  Every rank on this host pins its
+        # own buffers, so their size is planned against the host's free memory.
         del d_out
-        h_in = host_alloc(n * REC)
-        torch.from_numpy(h_in).view(n, REC).copy_(d_in)
+        ns, ne = e2e_plan(n, args.e2e_streams)
+        h_in = host_alloc(ne * REC)
+        torch.from_numpy(h_in).view(ne, REC).copy_(d_in[:ne])
         del d_in
         torch.cuda.empty_cache()
-        ns = max(1, args.e2e_streams)
-        h_outs = [host_alloc(n * REC) for _ in range(ns)]
+        h_outs = [host_alloc(ne * REC) for _ in range(ns)]
         addr_in = h_in.ctypes.data
         addr_out = [a.ctypes.data for a in h_outs]
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(ns - 1)]
         # warm-up: one sort queued on each stream (each gets its own scratch)
         for k in range(ns):
-            ley.ley_sort_records_async(addr_in, addr_out[k], n=n, rec_bytes=REC, key_bytes=kb,
+            ley.ley_sort_records_async(addr_in, addr_out[k], n=ne, rec_bytes=REC, key_bytes=kb,
                                        stream=streams[k])
         for st in streams:
             st.synchronize()
         lp0 = link_peaks(dev)  # the link before the steps (and again after them)
         # one blocking call: the latency of a single sort, host to host
         t0 = time.perf_counter()
-        ley.ley_sort_records(addr_in, addr_out[0], n=n, rec_bytes=REC, key_bytes=kb, stream=stream)
+        ley.ley_sort_records(addr_in, addr_out[0], n=ne, rec_bytes=REC, key_bytes=kb, stream=stream)
         lat = time.perf_counter() - t0
         # The timed steps, queued in turn on the streams: every step copies its
         # input in and its sorted records out, and one step's copy out
@@ -322,7 +323,7 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         barrier(pg, dev)
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            ley.ley_sort_records_async(addr_in, addr_out[k % ns], n=n, rec_bytes=REC,
+            ley.ley_sort_records_async(addr_in, addr_out[k % ns], n=ne, rec_bytes=REC,
                                        key_bytes=kb, stream=streams[k % ns])
         for st in streams:
             st.synchronize()
@@ -341,10 +342,10 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         # drift between and within processes.
         lp1 = link_peaks(dev)
         lp = {k: max(lp0[k], lp1[k]) for k in lp0}
-        floor_ms = n * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
-        e2e = {"value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s",
-               "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": n * REC,
-               "d2h_bytes_per_step": n * REC, "streams": ns,
+        floor_ms = ne * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
+        e2e = {"value": round(world * ne * REC / dt / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": world * ne * REC,
+               "d2h_bytes_per_step": world * ne * REC, "streams": ns, "records": ne,
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
                "link_before": lp0, "link_after": lp1,
                "duplex_floor_ms": round(floor_ms, 2),
@@ -637,6 +638,30 @@ def host_alloc(nbytes):
 def host_free(a):
     p = _HOST_BUFS.pop(a.ctypes.data)
     _libcuda().cuMemFreeHost(p)
+
+
+def e2e_plan(n, want_streams):
+    """(streams, records) for the end-to-end steps of this rank: the pinned
+    input plus one output per stream must fit in this rank's share of 60 % of
+    the host's available memory (every rank on the host pins its own).  Fewer
+    streams first, then fewer records."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    local = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    if avail is None:
+        return max(1, want_streams), n
+    share = 0.6 * avail / max(1, local) - 2 * (2 << 30)  # minus the link test's buffers
+    for ns in range(max(1, want_streams), 0, -1):
+        if (1 + ns) * n * REC <= share:
+            return ns, n
+    ne = int(share // (2 * REC)) // 4096 * 4096
+    return 1, max(4096, min(n, ne))
 
 
 def link_peaks(dev, nbytes=2 << 30, reps=3):

@@ -79,3 +79,21 @@ def test_reference_line_keeps_the_contract():
     assert out["e2e"]["value"] == out["value"] and out["e2e"]["unit"] == out["unit"]
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
     assert out["config"]["workload"].startswith("uniform_")
+
+
+def test_end_to_end_host_buffers_fit_each_ranks_share(monkeypatch):
+    # every rank on a host pins its own e2e buffers: their plan must fit the
+    # rank's share of the available memory, with fewer streams first
+    sys.path.insert(0, ROOT)
+    import bench
+    n = 100_000_000
+    for local in (1, 2, 8, 64):
+        monkeypatch.setenv("LOCAL_WORLD_SIZE", str(local))
+        ns, ne = bench.e2e_plan(n, 2)
+        assert 1 <= ns <= 2 and 4096 <= ne <= n
+        if ne < n:
+            assert ns == 1 and ne % 4096 == 0
+        with open("/proc/meminfo") as f:
+            avail = [int(l.split()[1]) * 1024 for l in f if l.startswith("MemAvailable:")][0]
+        share = 0.6 * avail / local
+        assert (1 + ns) * ne * bench.REC <= max(share, 2 * 4096 * bench.REC)
