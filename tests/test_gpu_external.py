@@ -84,6 +84,24 @@ def test_queued_partial_sorts_on_two_streams_exact(orc, ley):
         assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy()))
 
 
+def test_queued_long_key_sorts_on_two_streams_exact(orc, ley):
+    # keys longer than a tuple's 12 bytes (one sort per 12-byte window) in the
+    # queued partial mode, two sorts in flight on two streams
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    jobs = []
+    for i, (n, kb) in enumerate([(70_000, 30), (120_001, 17)]):
+        rec = datagen.ascii_records(n, seed=60 + i, key_bytes=kb, shared_prefix=9,
+                                    alphabet=4).pin_memory()
+        out = torch.zeros_like(rec).pin_memory()
+        ley.ley_sort_records_async(rec, out, key_bytes=kb, stream=streams[i])
+        jobs.append((rec, out, kb))
+    for st in streams:
+        st.synchronize()
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    for rec, out, kb in jobs:
+        assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy(), key_bytes=kb))
+
+
 def test_queued_sort_falls_back_to_blocking_external(orc, ley):
     # the budget is below the partial mode's need: the external sort runs and
     # the call returns with the records in place
