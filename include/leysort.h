@@ -218,6 +218,29 @@ ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
                                  uint64_t* hist_out, ley_stream_t stream);
 
 /*
+ * Partition planning of the external sort's merge (Section 3.2: the merge is
+ * cut into independent pieces for load balance): the merged order of k
+ * sorted runs, in the order (key, run, position) -- equal keys of a lower
+ * run first -- is cut into partitions of at most `cap` records by an exact
+ * k-way co-rank.  Host-only: no device work, and no GPU is needed.
+ *   runs[i]    host pointer to run i: run_len[i] records of rec_bytes bytes,
+ *              sorted stably by their first key_bytes bytes.
+ *   k          1..4096 runs (empty runs allowed).
+ *   cap        the largest partition, in records (>= 1).
+ *   cuts       out: *ncuts rows of k positions, row-major.  Row p holds, for
+ *              every run, the position at which partition p starts: row 0 is
+ *              all zeros, the last row is run_len, and partition p takes
+ *              records [cuts[p][i], cuts[p+1][i]) of every run i.
+ *   max_cuts   rows available in cuts; LEY_ENOMEM (with *ncuts set to the
+ *              rows needed) if more are needed.
+ * Partitions are about 3/4 of cap; their boundaries are exact, so merging
+ * each partition's slices alone and concatenating gives the full merge.
+ */
+ley_status ley_plan_partitions(const void* const* runs, const uint64_t* run_len, uint32_t k,
+                               uint32_t rec_bytes, uint32_t key_bytes, uint64_t cap,
+                               uint64_t* cuts, uint64_t max_cuts, uint64_t* ncuts);
+
+/*
  * K-way merge of sorted runs: the merge stage of the external sort
  * (Section 3.2, Figure 1: "a K-way merge algorithm"), exposed on its own.
  *   runs       device, run_start[k] records back to back; run r holds records

@@ -19,7 +19,8 @@ from . import build as _build
 
 __all__ = [
     "LeyError", "LEY_OK", "LEY_EINVAL", "LEY_ENOMEM", "LEY_EUNSUPPORTED", "LEY_ECUDA",
-    "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_records_async", "ley_sort_keys_index",
+    "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_records_async", "ley_plan_partitions",
+    "ley_sort_keys_index",
     "ley_partition_records",
     "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
@@ -89,6 +90,9 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_records.restype = ctypes.c_int
     lib.ley_sort_records_async.argtypes = [vp, vp, u64, u32, u32, u64, vp]
     lib.ley_sort_records_async.restype = ctypes.c_int
+    lib.ley_plan_partitions.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), u32, u32, u32,
+                                        u64, ctypes.POINTER(u64), u64, ctypes.POINTER(u64)]
+    lib.ley_plan_partitions.restype = ctypes.c_int
     lib.ley_sort_keys_index.argtypes = [vp, vp, vp, vp, u64, u64, vp]
     lib.ley_sort_keys_index.restype = ctypes.c_int
     lib.ley_partition_records.argtypes = [vp, u64, u32, u32, u32, vp, vp, vp]
@@ -212,6 +216,31 @@ def ley_sort_records_async(inp, out, n: int | None = None, rec_bytes: int | None
     st = _lib.ley_sort_records_async(_addr(inp), _addr(out), n, rec_bytes, key_bytes,
                                      mem_budget, _stream(stream, inp, out))
     return _check(st, "ley_sort_records_async")
+
+
+def ley_plan_partitions(runs, key_bytes: int = 10, cap: int = 1 << 20):
+    """Cut the merge of sorted host runs (uint8 [len_i, rec_bytes] numpy arrays)
+    into partitions of at most ``cap`` records; returns the cut positions as a
+    [partitions + 1, k] uint64 array.  See ``ley_plan_partitions`` in
+    include/leysort.h.  Host-only."""
+    import numpy as np
+    k = len(runs)
+    rec = int(runs[0].shape[1]) if k and runs[0].ndim == 2 else 100
+    ptrs = (ctypes.c_void_p * k)(*[r.ctypes.data if len(r) else 0 for r in runs])
+    lens = (ctypes.c_uint64 * k)(*[len(r) for r in runs])
+    need = ctypes.c_uint64(0)
+    rows = 2 + (sum(len(r) for r in runs) // max(1, cap // 2) + 2)
+    for _ in range(2):
+        cuts = np.zeros((rows, k), dtype=np.uint64)
+        st = _lib.ley_plan_partitions(ptrs, lens, k, rec, key_bytes, cap,
+                                      cuts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      rows, ctypes.byref(need))
+        if st == LEY_ENOMEM and need.value > rows:
+            rows = int(need.value)
+            continue
+        _check(st, "ley_plan_partitions")
+        return cuts[:need.value].copy()
+    raise LeyError(LEY_ENOMEM, "ley_plan_partitions")
 
 
 def ley_sort_records_batch(requests, rec_bytes: int = 100, key_bytes: int = 10,

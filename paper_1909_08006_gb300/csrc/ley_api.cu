@@ -1414,6 +1414,27 @@ ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
     return run_device_sort(a, 0, st);
 }
 
+ley_status ley_plan_partitions(const void* const* runs, const uint64_t* run_len, uint32_t k,
+                               uint32_t rec_bytes, uint32_t key_bytes, uint64_t cap,
+                               uint64_t* cuts, uint64_t max_cuts, uint64_t* ncuts) {
+    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 1 || rec_bytes > 4096)
+        return LEY_EUNSUPPORTED;
+    if (k < 1 || k > 4096 || cap < 1 || !run_len || !cuts || !ncuts || !runs) return LEY_EINVAL;
+    std::vector<HostRun> rs(k);
+    ull n = 0;
+    for (uint32_t i = 0; i < k; i++) {
+        if (run_len[i] && !runs[i]) return LEY_EINVAL;
+        rs[i] = {static_cast<const uint8_t*>(runs[i]), run_len[i]};
+        n += run_len[i];
+    }
+    const std::vector<std::vector<ull>> c = plan_partitions(rs, n, cap, rec_bytes, key_bytes);
+    *ncuts = c.size();
+    if (c.size() > max_cuts) return LEY_ENOMEM;
+    for (size_t p = 0; p < c.size(); p++)
+        for (uint32_t i = 0; i < k; i++) cuts[p * k + i] = c[p][i];
+    return LEY_OK;
+}
+
 ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32_t k, void* out,
                              uint32_t rec_bytes, uint32_t key_bytes, ley_stream_t stream) {
     if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
