@@ -75,9 +75,9 @@ typedef void* ley_stream_t;
  *               window at a time, least significant window first
  *               (ceil(key_bytes / 12) sorts, each stable on the order left by
  *               the windows after it); scratch grows by 12 bytes per record.
- *               Long keys are supported for device buffers and in the partial
- *               host mode; where the external mode would be needed,
- *               LEY_EUNSUPPORTED.
+ *               In the external mode each run and each merge partition is
+ *               sorted that way (a partition's slices, in run order, sorted
+ *               stably give its merge).
  *   mem_budget  cap on the library's device allocations in bytes, 0 = none.
  *   n           < 2^32.  n == 0 returns LEY_OK without touching the buffers.
  */

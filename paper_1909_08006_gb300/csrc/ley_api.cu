@@ -961,10 +961,17 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     const size_t stg_bytes = align_up(q * a.rec, 256);
     const size_t fixed = kStaging * stg_bytes + 64 * 1024;
     if (budget <= fixed) return LEY_ENOMEM;
-    // largest run (whole tiles) whose record buffers and workspaces fit
-    auto need = [&](ull r) {
-        return kExtBufs * (align_up(r * a.rec, 256) + make_layout(r, true).total) + fixed;
+    // Keys longer than a tuple's 12 bytes: each run, and each merge
+    // partition, is sorted window by window (its workspace grows by the two
+    // order arrays); the partitions are cut by the same exact co-rank on the
+    // whole key, so sorting a partition's slices stably -- ties in slice
+    // order, which is (run, position) -- gives its merge.
+    const bool long_key = a.kb > kWindow;
+    auto ws_bytes = [&](ull r) {
+        return make_layout(r, true).total + (long_key ? long_key_extra(r) : 0);
     };
+    // largest run (whole tiles) whose record buffers and workspaces fit
+    auto need = [&](ull r) { return kExtBufs * (align_up(r * a.rec, 256) + ws_bytes(r)) + fixed; };
     ull lo = 0, hi = a.n / kPassTile + 1;
     while (lo < hi) {
         const ull mid = (lo + hi + 1) / 2;
@@ -980,7 +987,8 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     if (k > 128) return LEY_ENOMEM;  // budget too small for the merge fan-in
     const Layout L = make_layout(r_len, true);
     const size_t in_bytes = align_up(r_len * a.rec, 256);
-    const size_t total = kExtBufs * (in_bytes + L.total) + kStaging * stg_bytes + 8 * 1024;
+    const size_t ws_len = ws_bytes(r_len);
+    const size_t total = kExtBufs * (in_bytes + ws_len) + kStaging * stg_bytes + 8 * 1024;
     const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
     if (dbg)
         std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
@@ -996,9 +1004,14 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     char* ws[kExtBufs];
     for (int i = 0; i < kExtBufs; i++) {
         dbuf[i] = reinterpret_cast<uint8_t*>(base + i * in_bytes);
-        ws[i] = base + kExtBufs * in_bytes + i * L.total;
+        ws[i] = base + kExtBufs * in_bytes + i * ws_len;
     }
-    char* tail = base + kExtBufs * (in_bytes + L.total);
+    // the two order arrays of a long-key sort of up to r_len records in ws[b]
+    auto long_ord = [&](int b, uint32_t** ord) {
+        ord[0] = reinterpret_cast<uint32_t*>(ws[b] + L.total);
+        ord[1] = reinterpret_cast<uint32_t*>(ws[b] + L.total + long_key_extra(r_len) / 2);
+    };
+    char* tail = base + kExtBufs * (in_bytes + ws_len);
     uint8_t* stg[kStaging];
     for (int i = 0; i < kStaging; i++) stg[i] = reinterpret_cast<uint8_t*>(tail + i * stg_bytes);
     ull* off_dev = reinterpret_cast<ull*>(tail + kStaging * stg_bytes);
@@ -1023,13 +1036,26 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
             ra.n = rn;
             Work w = make_work(ws[b], L, rn, ds->err);
             hp.mark(hp.h2d, "run in begin", r);
-            if (s == LEY_OK) s = stage_prepare(w, L, st, rn, 0);
-            if (s == LEY_OK) s = stream_in_extract(ra, a.in + r0 * a.rec, dbuf[b], w, ks, st, hp, ds->sms);
-            hp.mark(hp.h2d, "run in end", r);
-            if (s == LEY_OK) s = stage_levels_finish(ra, w, ks, st, ds->sms);
+            const uint32_t* order = w.perm;
+            if (long_key) {  // the whole run first, then one sort per 12-byte window
+                if (s == LEY_OK && cudaMemcpyAsync(dbuf[b], a.in + r0 * a.rec, rn * a.rec,
+                                                   cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+                    s = LEY_ECUDA;
+                if (s == LEY_OK && !hp.order(hp.h2d, st)) s = LEY_ECUDA;
+                hp.mark(hp.h2d, "run in end", r);
+                uint32_t* ord[2];
+                long_ord(b, ord);
+                if (s == LEY_OK) s = enqueue_long_key_order(ra, w, L, ord, st, ds->sms, &order);
+            } else {
+                if (s == LEY_OK) s = stage_prepare(w, L, st, rn, 0);
+                if (s == LEY_OK)
+                    s = stream_in_extract(ra, a.in + r0 * a.rec, dbuf[b], w, ks, st, hp, ds->sms);
+                hp.mark(hp.h2d, "run in end", r);
+                if (s == LEY_OK) s = stage_levels_finish(ra, w, ks, st, ds->sms);
+            }
             hp.mark(st, "run sorted", r);
             if (s == LEY_OK && !hp.order(st, hp.gth)) s = LEY_ECUDA;
-            if (s == LEY_OK) s = stream_out(ra, w.perm, 0, rn, hs + r0 * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+            if (s == LEY_OK) s = stream_out(ra, order, 0, rn, hs + r0 * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
             hp.mark(hp.gth, "run gathered", r);
             hp.mark(hp.d2h, "run out end", r);
             if (s == LEY_OK && !(buf_free[b] = hp.record(hp.gth))) s = LEY_ECUDA;
@@ -1072,10 +1098,17 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
             SortArgs ma = a;
             ma.in = dbuf[b];
             ma.n = m;
-            if (s == LEY_OK) s = stage_merge(ma, dbuf[b], off.data(), off_dev, k, w, L, st, ds->sms);
+            const uint32_t* order = w.perm;
+            if (long_key) {  // the slices in (run, position) order, sorted stably
+                uint32_t* ord[2];
+                long_ord(b, ord);
+                if (s == LEY_OK) s = enqueue_long_key_order(ma, w, L, ord, st, ds->sms, &order);
+            } else {
+                if (s == LEY_OK) s = stage_merge(ma, dbuf[b], off.data(), off_dev, k, w, L, st, ds->sms);
+            }
             hp.mark(st, "part merged", (long)p);
             if (s == LEY_OK && !hp.order(st, hp.gth)) s = LEY_ECUDA;
-            if (s == LEY_OK) s = stream_out(ma, w.perm, 0, m, a.out + out_pos * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+            if (s == LEY_OK) s = stream_out(ma, order, 0, m, a.out + out_pos * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
             hp.mark(hp.gth, "part gathered", (long)p);
             hp.mark(hp.d2h, "part out end", (long)p);
             if (s == LEY_OK && !(buf_free[b] = hp.record(hp.gth))) s = LEY_ECUDA;
@@ -1191,7 +1224,6 @@ static ley_status run_host_sort(const SortArgs& a, ull budget, cudaStream_t st,
         s = run_host_keys_only(a, budget, st);
         if (s != LEY_ENOMEM) return s;
     }
-    if (a.kb > kWindow) return LEY_EUNSUPPORTED;  // the merge compares 12-byte tuples
     return run_host_external(a, budget, st);
 }
 

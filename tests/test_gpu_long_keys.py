@@ -68,13 +68,22 @@ def test_long_keys_partial_host_mode(orc, ley):
     assert np.array_equal(h_out.numpy(), orc.sort_records(rec.numpy(), key_bytes=30))
 
 
-def test_long_keys_unsupported_paths(ley):
-    rec = datagen.uniform_records(100_000, seed=1)
+@pytest.mark.parametrize("n,kb,budget", [(200_003, 20, 10 << 20), (120_000, 37, 8 << 20)])
+def test_long_keys_external_mode_exact(orc, ley, n, kb, budget):
+    # a budget below the partial mode's need: runs and merge partitions are
+    # each sorted window by window; few symbols and a shared prefix put ties
+    # across runs and across partition cuts
+    rec = datagen.ascii_records(n, seed=kb, key_bytes=kb, shared_prefix=8, alphabet=3)
+    assert ley.ley_workspace_bytes(n, key_bytes=kb) + n * 100 > budget
     h_in = rec.pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
-    with pytest.raises(ley.LeyError) as e:  # external mode: the merge compares 12-byte tuples
-        ley.ley_sort_records(h_in, h_out, key_bytes=20, mem_budget=6 << 20)
-    assert e.value.status == ley.LEY_EUNSUPPORTED
+    ley.ley_sort_records(h_in, h_out, key_bytes=kb, mem_budget=budget)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    assert np.array_equal(h_out.numpy(), orc.sort_records(rec.numpy(), key_bytes=kb))
+
+
+def test_long_keys_unsupported_paths(ley):
+    rec = datagen.uniform_records(100_000, seed=1)
     d = rec.to(DEV)
     with pytest.raises(ley.LeyError) as e:
         ley.ley_sort_records_batch([(d, torch.empty_like(d))], key_bytes=20)
