@@ -24,6 +24,22 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(ley_[a-z_]+)\s*\(", text)))
 
 
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header alone compiles as C99, with no C++
+    # or PyTorch types
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "leysort.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", os.path.dirname(HEADER), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["ley_sort_records", "ley_sort_keys_index", "ley_partition_records",
