@@ -191,7 +191,8 @@ def run_ours(args, world, rank, local, pg):
     stream = torch.cuda.Stream(dev)
     wl = args.workload
     tuning = None
-    if args.autotune:
+    if args.autotune and wl not in ("uniform", "skew", "ascii"):
+        # the record workloads tune on their own data (in _run_workload)
         tuning = ley.ley_autotune_records(min(n, 100_000_000), REC, KEY)
     out = _run_workload(args, world, rank, local, pg, dev, stream, wl, n)
     if out is not None:
@@ -218,8 +219,10 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
     else:
         gen = datagen.skew_records if wl == "skew" else datagen.uniform_records
         d_in = gen(n, seed=2 if wl == "uniform" else 3, device=dev)
-    d_out = torch.empty_like(d_in)
     torch.cuda.synchronize()
+    if args.autotune:  # the thresholds that sort this workload's own records fastest
+        ley.ley_autotune_records_on(d_in, n=n, rec_bytes=REC, key_bytes=kb)
+    d_out = torch.empty_like(d_in)
 
     def step():
         ley.ley_sort_records(d_in, d_out, n=n, rec_bytes=REC, key_bytes=kb, stream=stream)

@@ -305,6 +305,16 @@ ley_status ley_set_tuning(const ley_tuning* tuning);
 ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
                                 uint64_t seed, ley_tuning* best);
 
+/*
+ * The same autotuner on the caller's own records: `in` is n records of
+ * rec_bytes on the device (16-byte aligned), read and never written; the
+ * timed sorts go to scratch of n * rec_bytes bytes.  Thresholds that suit
+ * one key distribution (say uniform) can be slower on another (say skewed),
+ * so tuning on the data to be sorted is the reliable form.  Blocks.
+ */
+ley_status ley_autotune_records_on(const void* in, uint64_t n, uint32_t rec_bytes,
+                                   uint32_t key_bytes, ley_tuning* best);
+
 /* Static English text for a status code (never NULL). */
 const char* ley_status_string(ley_status s);
 

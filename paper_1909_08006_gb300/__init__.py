@@ -28,7 +28,8 @@ __all__ = [
     "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
     "ley_server_create", "ley_server_submit_records", "ley_server_submit_pairs",
     "ley_server_wait", "ley_server_stats", "ley_server_destroy",
-    "ley_get_tuning", "ley_set_tuning", "ley_autotune_records", "ley_selftest_timeout",
+    "ley_get_tuning", "ley_set_tuning", "ley_autotune_records", "ley_autotune_records_on",
+    "ley_selftest_timeout",
 ]
 
 LEY_OK, LEY_EINVAL, LEY_ENOMEM, LEY_EUNSUPPORTED, LEY_ECUDA, LEY_ETIMEOUT = range(6)
@@ -127,6 +128,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_set_tuning.restype = ctypes.c_int
     lib.ley_autotune_records.argtypes = [u64, u32, u32, u64, ctypes.POINTER(_Tuning)]
     lib.ley_autotune_records.restype = ctypes.c_int
+    lib.ley_autotune_records_on.argtypes = [vp, u64, u32, u32, ctypes.POINTER(_Tuning)]
+    lib.ley_autotune_records_on.restype = ctypes.c_int
     lib.ley_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
     lib.ley_server_create.restype = ctypes.c_int
     lib.ley_server_submit_records.argtypes = [vp, vp, vp, u64, u32, u32, ctypes.POINTER(u64)]
@@ -311,6 +314,20 @@ def ley_autotune_records(n: int, rec_bytes: int = 100, key_bytes: int = 10,
     t = _Tuning()
     _check(_lib.ley_autotune_records(n, rec_bytes, key_bytes, seed, ctypes.byref(t)),
            "ley_autotune_records")
+    return {f: int(getattr(t, f)) for f, _ in _Tuning._fields_}
+
+
+def ley_autotune_records_on(inp, n: int | None = None, rec_bytes: int | None = None,
+                            key_bytes: int = 10) -> dict:
+    """Times a grid of tunings on the caller's device records (a uint8
+    [n, rec_bytes] tensor, not modified); keeps and returns the fastest."""
+    if n is None:
+        n = int(inp.shape[0])
+    if rec_bytes is None:
+        rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
+    t = _Tuning()
+    _check(_lib.ley_autotune_records_on(_addr(inp), n, rec_bytes, key_bytes, ctypes.byref(t)),
+           "ley_autotune_records_on")
     return {f: int(getattr(t, f)) for f, _ in _Tuning._fields_}
 
 

@@ -1549,26 +1549,17 @@ ley_status ley_set_tuning(const ley_tuning* t) {
     return LEY_OK;
 }
 
-ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
-                                uint64_t seed, ley_tuning* best) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
-        return LEY_EUNSUPPORTED;
-    DevState* ds = dev_state();
-    if (!ds) return LEY_ECUDA;
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEY_ECUDA;
-    const ull bytes = n * rec_bytes;
-    void *in = nullptr, *out = nullptr;
+}  // extern "C"
+
+namespace ley {
+// Times sorts of the n records at `in` (device) into `out` under a grid of
+// tunings -- Algorithm 1's two thresholds and the finishing CTAs per SM; the
+// first candidate is the default -- keeps the fastest (best of two timed
+// sorts after one warm-up) as the current tuning and returns it.
+static ley_status autotune_on(const void* in, void* out, ull n, uint32_t rec_bytes,
+                              uint32_t key_bytes, cudaStream_t st, ley_tuning* best) {
     ley_status s = LEY_OK;
-    if (!scratch_alloc(ds, &in, align_up(bytes, 256), st) ||
-        !scratch_alloc(ds, &out, align_up(bytes, 256), st))
-        s = LEY_ENOMEM;
-    if (s == LEY_OK && launch_fill_random(st, static_cast<uint8_t*>(in), bytes, seed) != cudaSuccess)
-        s = LEY_ECUDA;
     const Tuning saved = cur_tuning();
-    // Algorithm 1's two thresholds and the CTAs per SM of the two heaviest
-    // kernels; the first candidate is the default.
     std::vector<Tuning> cands;
     for (uint32_t big : {2048u, 1536u, 1024u})
         for (uint32_t tiny : {32u, 64u, 128u})
@@ -1580,8 +1571,7 @@ ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_byt
                 cands.push_back(c);
             }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (s == LEY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-        s = LEY_ECUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = LEY_ECUDA;
     float best_ms = 1e30f;
     Tuning best_t = cands[0];
     for (size_t i = 0; i < cands.size() && s == LEY_OK; i++) {
@@ -1621,7 +1611,52 @@ ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_byt
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    return s;
+}
+}  // namespace ley
+
+extern "C" {
+
+ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                                uint64_t seed, ley_tuning* best) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
+        return LEY_EUNSUPPORTED;
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEY_ECUDA;
+    const ull bytes = n * rec_bytes;
+    void *in = nullptr, *out = nullptr;
+    ley_status s = LEY_OK;
+    if (!scratch_alloc(ds, &in, align_up(bytes, 256), st) ||
+        !scratch_alloc(ds, &out, align_up(bytes, 256), st))
+        s = LEY_ENOMEM;
+    if (s == LEY_OK && launch_fill_random(st, static_cast<uint8_t*>(in), bytes, seed) != cudaSuccess)
+        s = LEY_ECUDA;
+    if (s == LEY_OK) s = autotune_on(in, out, n, rec_bytes, key_bytes, st, best);
     if (in) cudaFreeAsync(in, st);
+    if (out) cudaFreeAsync(out, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return s;
+}
+
+ley_status ley_autotune_records_on(const void* in, uint64_t n, uint32_t rec_bytes,
+                                   uint32_t key_bytes, ley_tuning* best) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
+        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
+        return LEY_EUNSUPPORTED;
+    if (!in) return LEY_EINVAL;
+    if (mem_kind(in) != MK_DEVICE || !aligned16(in)) return LEY_EINVAL;
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEY_ECUDA;
+    void* out = nullptr;
+    ley_status s = LEY_OK;
+    if (!scratch_alloc(ds, &out, align_up(n * rec_bytes, 256), st)) s = LEY_ENOMEM;
+    if (s == LEY_OK) s = autotune_on(in, out, n, rec_bytes, key_bytes, st, best);
     if (out) cudaFreeAsync(out, st);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);

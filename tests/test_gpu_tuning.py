@@ -85,3 +85,24 @@ def test_autotuner_picks_a_candidate_and_stays_exact(orc, ley):
         assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(rec.numpy()))
     finally:
         ley.ley_set_tuning(None)
+
+
+def test_autotuner_on_callers_records_leaves_them_and_stays_exact(orc, ley):
+    # tuning on the data to be sorted: the records are read, never written
+    try:
+        rec = datagen.skew_records(400_000, seed=12)
+        d_in = rec.to(DEV)
+        before = d_in.clone()
+        best = ley.ley_autotune_records_on(d_in, key_bytes=10)
+        assert torch.equal(d_in, before)
+        assert best["big_bucket"] in (2048, 1536, 1024)
+        assert best["tiny_bucket"] in (32, 64, 128)
+        assert ley.ley_get_tuning() == best
+        d_out = torch.empty_like(d_in)
+        ley.ley_sort_records(d_in, d_out)
+        assert np.array_equal(d_out.cpu().numpy(), orc.sort_records(rec.numpy()))
+        with pytest.raises(ley.LeyError) as e:  # host memory is not a device record array
+            ley.ley_autotune_records_on(rec.pin_memory(), key_bytes=10)
+        assert e.value.status == ley.LEY_EINVAL
+    finally:
+        ley.ley_set_tuning(None)
