@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", _SRC, "-o", tmp]
+    base = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-pthread", _SRC,
+            "-o", tmp]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)
@@ -54,6 +55,10 @@ def _load():
             lib.oracle_sort_records.restype = ctypes.c_int
             lib.oracle_sort_records.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, u64p]
+            lib.oracle_sort_records_threads.restype = ctypes.c_int
+            lib.oracle_sort_records_threads.argtypes = [u8p, u8p, ctypes.c_uint64,
+                                                        ctypes.c_uint32, ctypes.c_uint32,
+                                                        ctypes.c_uint32]
             lib.oracle_sort_keys_index.restype = ctypes.c_int
             lib.oracle_sort_keys_index.argtypes = [u64p, u32p, u64p, u32p, ctypes.c_uint64]
             lib.oracle_digit_histogram.restype = None
@@ -78,6 +83,10 @@ def _load():
             lib.oracle_check_tagged.restype = ctypes.c_int64
             lib.oracle_check_tagged.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, ctypes.c_uint32]
+            lib.oracle_check_tagged_threads.restype = ctypes.c_int64
+            lib.oracle_check_tagged_threads.argtypes = [u8p, u8p, ctypes.c_uint64,
+                                                        ctypes.c_uint32, ctypes.c_uint32,
+                                                        ctypes.c_uint32, ctypes.c_uint32]
             lib.oracle_check_pairs_tagged.restype = ctypes.c_int64
             lib.oracle_check_pairs_tagged.argtypes = [u64p, u32p, u64p, ctypes.c_uint64]
             _lib = lib
@@ -107,6 +116,20 @@ def sort_records(records, key_bytes: int = 10, return_perm: bool = False):
     if rc != 0:
         raise MemoryError("oracle_sort_records: out of memory")
     return (out, perm[:n]) if return_perm else out
+
+
+def sort_records_threads(records, key_bytes: int = 10, threads: int | None = None):
+    """The same sort on ``threads`` host threads (default: every core):
+    contiguous chunks sorted in parallel, a T-way heap merge, a parallel
+    record copy.  For the CPU baseline; equal to ``sort_records``."""
+    a = _records(records)
+    n, rec = a.shape
+    T = threads if threads else (os.cpu_count() or 1)
+    out = np.empty_like(a)
+    rc = _load().oracle_sort_records_threads(_ptr(a, u8p), _ptr(out, u8p), n, rec, key_bytes, T)
+    if rc != 0:
+        raise MemoryError(f"oracle_sort_records_threads failed ({rc})")
+    return out
 
 
 def sort_keys_index(keys, idx):
@@ -179,6 +202,17 @@ def check_tagged(out, inp, key_bytes: int = 10, tag_offset: int = 10) -> int:
     assert o.shape == i.shape
     return int(_load().oracle_check_tagged(_ptr(o, u8p), _ptr(i, u8p), o.shape[0], o.shape[1],
                                            key_bytes, tag_offset))
+
+
+def check_tagged_threads(out, inp, key_bytes: int = 10, tag_offset: int = 10,
+                         threads: int | None = None) -> int:
+    """check_tagged on ``threads`` host threads (default: every core): -1 if
+    exact, else a bad output position."""
+    o, i = _records(out), _records(inp)
+    assert o.shape == i.shape
+    T = threads if threads else (os.cpu_count() or 1)
+    return int(_load().oracle_check_tagged_threads(_ptr(o, u8p), _ptr(i, u8p), o.shape[0],
+                                                   o.shape[1], key_bytes, tag_offset, T))
 
 
 def check_pairs_tagged(keys_out, idx_out, keys_in) -> int:

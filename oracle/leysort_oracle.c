@@ -25,6 +25,7 @@
  * itself: brute force over all permutations, numpy's stable lexsort, the
  * worked partition example of Section 2.2, planted mistakes and invariants.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -95,6 +96,190 @@ ORACLE_API int oracle_sort_keys_index(const uint64_t* keys_in, const uint32_t* i
     }
     free(idx);
     return 0;
+}
+
+/* ------------------------------------------ the same sort on T threads */
+
+/* The sort of oracle_sort_records on T host threads, the multi-core form of
+ * the CPU baseline (it is timed, never used to produce expected values).
+ *  1. The input is cut into T contiguous index ranges ("chunks"); each thread
+ *     sorts its chunk's (key, index) order with the same comparison.
+ *  2. T-1 pivots split the merged order into T pieces: 32 evenly spaced
+ *     elements of every sorted chunk are sorted together and every 32nd is
+ *     taken (the classic sample split of a parallel merge).
+ *  3. Thread t merges piece t: in every chunk, the elements from pivot t
+ *     (inclusive) to pivot t+1 (exclusive), found by binary search, by a
+ *     binary min-heap of sub-range heads (the textbook T-way merge), into the
+ *     output positions that follow all elements below pivot t.
+ *  4. T threads copy the records into place.
+ * The chunks are contiguous and every comparison includes the index, so the
+ * order is exactly the single-threaded one. */
+#define SAMPLES_PER_CHUNK 32
+
+typedef struct {
+    const uint8_t* in;
+    uint8_t* out;
+    uint64_t* idx;          /* sorted chunks, in place */
+    uint64_t* perm;         /* merged order */
+    const uint64_t* cb;     /* chunk boundaries, T + 1 entries */
+    const uint64_t* pivot;  /* T + 1 entries: pivot t is an element index; entries 0 and T
+                               are unused (no lower, no upper bound) */
+    uint64_t lo, hi;        /* this thread's chunk (step 1) or output range (step 4) */
+    uint32_t t, T, rec, key;
+} par_job;
+
+static void* sort_chunk(void* arg) {
+    par_job* j = (par_job*)arg;
+    for (uint64_t i = j->lo; i < j->hi; i++) j->idx[i] = i;
+    rec_ctx c = {j->in, j->rec, j->key};
+    qsort_r(j->idx + j->lo, j->hi - j->lo, sizeof(uint64_t), cmp_record_index, &c);
+    return NULL;
+}
+
+/* First position in sorted idx[lo, hi) whose element is not below element v. */
+static uint64_t lower_bound_idx(const uint64_t* idx, uint64_t lo, uint64_t hi, uint64_t v,
+                                rec_ctx* c) {
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (cmp_record_index(&idx[mid], &v, c) < 0) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+static void sift_down(const uint64_t* idx, const uint64_t* pos, uint32_t* heap, uint32_t size,
+                      uint32_t i, rec_ctx* c) {
+    for (;;) {
+        uint32_t m = i, l = 2 * i + 1, r = 2 * i + 2;
+        if (l < size && cmp_record_index(&idx[pos[heap[l]]], &idx[pos[heap[m]]], c) < 0) m = l;
+        if (r < size && cmp_record_index(&idx[pos[heap[r]]], &idx[pos[heap[m]]], c) < 0) m = r;
+        if (m == i) return;
+        uint32_t tmp = heap[i];
+        heap[i] = heap[m];
+        heap[m] = tmp;
+        i = m;
+    }
+}
+
+static void* merge_piece(void* arg) {
+    par_job* j = (par_job*)arg;
+    const uint32_t T = j->T, t = j->t;
+    rec_ctx c = {j->in, j->rec, j->key};
+    uint64_t* pos = (uint64_t*)malloc(T * sizeof(uint64_t));
+    uint64_t* end = (uint64_t*)malloc(T * sizeof(uint64_t));
+    uint32_t* heap = (uint32_t*)malloc(T * sizeof(uint32_t));
+    if (!pos || !end || !heap) {
+        free(pos);
+        free(end);
+        free(heap);
+        j->lo = 1;  /* failure flag */
+        return NULL;
+    }
+    uint64_t out = 0;  /* elements of all chunks below pivot t */
+    for (uint32_t i = 0; i < T; i++) {
+        const uint64_t a = j->cb[i], b = j->cb[i + 1];
+        pos[i] = t == 0 ? a : lower_bound_idx(j->idx, a, b, j->pivot[t], &c);
+        end[i] = t + 1 == T ? b : lower_bound_idx(j->idx, a, b, j->pivot[t + 1], &c);
+        out += pos[i] - a;
+    }
+    uint32_t size = 0;
+    for (uint32_t i = 0; i < T; i++)
+        if (pos[i] < end[i]) heap[size++] = i;
+    for (uint32_t i = size / 2; i-- > 0;) sift_down(j->idx, pos, heap, size, i, &c);
+    while (size) {
+        const uint32_t i = heap[0];
+        j->perm[out++] = j->idx[pos[i]++];
+        if (pos[i] == end[i]) heap[0] = heap[--size];
+        if (size) sift_down(j->idx, pos, heap, size, 0, &c);
+    }
+    free(pos);
+    free(end);
+    free(heap);
+    j->lo = 0;
+    return NULL;
+}
+
+static void* copy_range(void* arg) {
+    par_job* j = (par_job*)arg;
+    for (uint64_t i = j->lo; i < j->hi; i++)
+        memcpy(j->out + i * j->rec, j->in + j->perm[i] * j->rec, j->rec);
+    return NULL;
+}
+
+/* Runs fn on jobs[0..T) in T threads; -2 if a thread cannot be started. */
+static int run_threads(void* (*fn)(void*), par_job* jobs, pthread_t* th, uint32_t T) {
+    for (uint32_t t = 0; t < T; t++)
+        if (pthread_create(&th[t], NULL, fn, &jobs[t]) != 0) {
+            for (uint32_t u = 0; u < t; u++) pthread_join(th[u], NULL);
+            return -2;
+        }
+    for (uint32_t t = 0; t < T; t++) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* Sorts n records on T threads: out[j] = in[perm[j]] with the permutation of
+ * oracle_sort_records.  Returns 0, -1 if memory runs out, -2 if a thread
+ * cannot be started. */
+ORACLE_API int oracle_sort_records_threads(const uint8_t* in, uint8_t* out, uint64_t n,
+                                           uint32_t rec_bytes, uint32_t key_bytes,
+                                           uint32_t threads) {
+    uint32_t T = threads ? threads : 1;
+    if ((uint64_t)T > n) T = n ? (uint32_t)n : 1;
+    const uint64_t ns = (uint64_t)T * SAMPLES_PER_CHUNK;
+    uint64_t* idx = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint64_t* perm = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint64_t* cb = (uint64_t*)malloc((T + 1) * sizeof(uint64_t));
+    uint64_t* pivot = (uint64_t*)malloc((T + 1) * sizeof(uint64_t));
+    uint64_t* samp = (uint64_t*)malloc(ns * sizeof(uint64_t));
+    pthread_t* th = (pthread_t*)malloc(T * sizeof(pthread_t));
+    par_job* jobs = (par_job*)malloc(T * sizeof(par_job));
+    int rc = 0;
+    if (!idx || !perm || !cb || !pivot || !samp || !th || !jobs) {
+        rc = -1;
+        goto done;
+    }
+    for (uint32_t t = 0; t <= T; t++) cb[t] = n * t / T;
+    for (uint32_t t = 0; t < T; t++) {
+        par_job j = {in, out, idx, perm, cb, pivot, cb[t], cb[t + 1], t, T, rec_bytes, key_bytes};
+        jobs[t] = j;
+    }
+    /* 1. chunks sorted in parallel */
+    if ((rc = run_threads(sort_chunk, jobs, th, T)) != 0) goto done;
+    /* 2. pivots from evenly spaced samples of the sorted chunks */
+    {
+        uint64_t m = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            const uint64_t len = cb[t + 1] - cb[t];
+            for (uint32_t k = 0; k < SAMPLES_PER_CHUNK && len; k++)
+                samp[m++] = idx[cb[t] + len * k / SAMPLES_PER_CHUNK];
+        }
+        rec_ctx c = {in, rec_bytes, key_bytes};
+        qsort_r(samp, m, sizeof(uint64_t), cmp_record_index, &c);
+        pivot[0] = pivot[T] = 0;
+        for (uint32_t t = 1; t < T; t++) pivot[t] = samp[m * t / T];
+    }
+    /* 3. the T pieces of the merge, in parallel */
+    if ((rc = run_threads(merge_piece, jobs, th, T)) != 0) goto done;
+    for (uint32_t t = 0; t < T; t++)
+        if (jobs[t].lo != 0) {
+            rc = -1;
+            goto done;
+        }
+    /* 4. the records copied into place in parallel */
+    for (uint32_t t = 0; t < T; t++) {
+        jobs[t].lo = cb[t];
+        jobs[t].hi = cb[t + 1];
+    }
+    rc = run_threads(copy_range, jobs, th, T);
+done:
+    free(idx);
+    free(perm);
+    free(cb);
+    free(pivot);
+    free(samp);
+    free(th);
+    free(jobs);
+    return rc;
 }
 
 /* ------------------------------------------------- one round of Alg. 1 */
@@ -243,6 +428,87 @@ ORACLE_API int64_t oracle_check_tagged(const uint8_t* out, const uint8_t* in, ui
         prev_tag = t;
     }
     free(seen);
+    return bad;
+}
+
+/* The check of oracle_check_tagged on T host threads (for full-size
+ * outputs): thread t checks output positions [n t / T, n (t + 1) / T), each
+ * position against its predecessor (across range boundaries too), and marks
+ * tags with an atomic exchange so that a tag seen twice is caught whichever
+ * thread sees it second.  Returns -1 if the output is exact, else a bad
+ * position (the first one a thread found; with a duplicated tag, either
+ * occurrence). */
+typedef struct {
+    const uint8_t *out, *in;
+    uint8_t* seen;
+    uint64_t n, lo, hi;
+    uint32_t rec, key, tag_off;
+    int64_t bad;
+} check_job;
+
+static void* check_range(void* arg) {
+    check_job* c = (check_job*)arg;
+    c->bad = -1;
+    for (uint64_t j = c->lo; j < c->hi; j++) {
+        const uint8_t* o = c->out + j * c->rec;
+        const uint8_t* q = o + c->tag_off;
+        const uint32_t t = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) |
+                           ((uint32_t)q[3] << 24);
+        if (t >= c->n || __atomic_exchange_n(&c->seen[t], (uint8_t)1, __ATOMIC_RELAXED)) {
+            c->bad = (int64_t)j;
+            return NULL;
+        }
+        if (memcmp(o, c->in + (uint64_t)t * c->rec, c->rec) != 0) {
+            c->bad = (int64_t)j;
+            return NULL;
+        }
+        if (j > 0) {
+            const uint8_t* p = o - c->rec;
+            const uint8_t* pq = p + c->tag_off;
+            const uint32_t pt = (uint32_t)pq[0] | ((uint32_t)pq[1] << 8) |
+                                ((uint32_t)pq[2] << 16) | ((uint32_t)pq[3] << 24);
+            const int cm = memcmp(p, o, c->key);
+            if (cm > 0 || (cm == 0 && pt >= t)) {
+                c->bad = (int64_t)j;
+                return NULL;
+            }
+        }
+    }
+    return NULL;
+}
+
+ORACLE_API int64_t oracle_check_tagged_threads(const uint8_t* out, const uint8_t* in, uint64_t n,
+                                               uint32_t rec_bytes, uint32_t key_bytes,
+                                               uint32_t tag_off, uint32_t threads) {
+    uint32_t T = threads ? threads : 1;
+    if ((uint64_t)T > n) T = n ? (uint32_t)n : 1;
+    uint8_t* seen = (uint8_t*)calloc(n ? n : 1, 1);
+    pthread_t* th = (pthread_t*)malloc(T * sizeof(pthread_t));
+    check_job* jobs = (check_job*)malloc(T * sizeof(check_job));
+    int64_t bad = -1;
+    if (!seen || !th || !jobs) {
+        bad = (int64_t)n;
+        goto done;
+    }
+    uint32_t started = 0;
+    for (uint32_t t = 0; t < T; t++) {
+        check_job c = {out, in, seen, n, n * t / T, n * (t + 1) / T, rec_bytes, key_bytes,
+                       tag_off, -1};
+        jobs[t] = c;
+    }
+    for (; started < T; started++)
+        if (pthread_create(&th[started], NULL, check_range, &jobs[started]) != 0) break;
+    for (uint32_t t = 0; t < started; t++) pthread_join(th[t], NULL);
+    if (started < T) {
+        bad = (int64_t)n;  /* could not check everything */
+        goto done;
+    }
+    for (uint32_t t = 0; t < T; t++)
+        if (jobs[t].bad >= 0 && (bad < 0 || jobs[t].bad < bad)) bad = jobs[t].bad;
+done:
+    free(seen);
+    free(th);
+    free(jobs);
     return bad;
 }
 

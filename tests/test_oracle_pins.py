@@ -197,6 +197,27 @@ def test_checkers_catch_planted_mistakes(orc):
     bad = out.copy()
     bad[7] = bad[6]
     assert orc.check_tagged(bad, a) >= 0
+    # the threaded form of the same check catches the same mistakes, also
+    # across its range boundaries
+    for T in (1, 3, 8):
+        assert orc.check_tagged_threads(out, a, threads=T) == -1
+        b2 = out.copy()
+        b2[5, 50] ^= 1
+        assert orc.check_tagged_threads(b2, a, threads=T) == 5
+        b2 = out.copy()
+        b2[[j, j + 1]] = b2[[j + 1, j]]
+        assert orc.check_tagged_threads(b2, a, threads=T) == j + 1
+        b2 = out.copy()
+        b2[7] = b2[6]
+        assert orc.check_tagged_threads(b2, a, threads=T) in (6, 7)
+        b2 = out.copy()
+        b2[[10, 3000]] = b2[[3000, 10]]
+        assert orc.check_tagged_threads(b2, a, threads=T) >= 0
+        cut = len(out) // T  # an order mistake exactly at a range boundary
+        if T > 1 and cut + 1 < len(out):
+            b2 = out.copy()
+            b2[[cut - 1, cut]] = b2[[cut, cut - 1]]  # tags differ: key or tag order breaks
+            assert orc.check_tagged_threads(b2, a, threads=T) >= 0
 
 
 def test_pair_checker_catches_planted_mistakes(orc):
@@ -212,3 +233,26 @@ def test_pair_checker_catches_planted_mistakes(orc):
     kb = ko.copy()
     kb[100] ^= 1
     assert orc.check_pairs_tagged(kb, vo, k) >= 0
+
+
+# ------------------------------------------------ the T-thread baseline
+
+@pytest.mark.parametrize("n,threads", [(0, 4), (1, 4), (5, 8), (1000, 1), (1000, 3),
+                                       (20_011, 7), (50_000, 16), (4096, 64)])
+def test_threaded_sort_equals_lexsort(orc, n, threads):
+    # chunked sorts + T-way heap merge: the same unique order as numpy's
+    # stable lexsort (ties by index), on tie-heavy and on distinct keys
+    for alphabet in (b"AB", None):
+        a = rand_records(n, rec=13, key=9, seed=n + threads, alphabet=alphabet)
+        got = orc.sort_records_threads(a, key_bytes=9, threads=threads)
+        assert np.array_equal(got, a[lex_perm(a, 9)])
+        assert np.array_equal(got, orc.sort_records(a, key_bytes=9))
+
+
+def test_threaded_sort_catches_a_merge_tie_error(orc):
+    # every chunk holds the same key: the merge must take equal heads in
+    # chunk order (the index decides), or the payload order changes
+    a = rand_records(3000, rec=12, key=4, seed=3)
+    a[:, :4] = 7
+    got = orc.sort_records_threads(a, key_bytes=4, threads=5)
+    assert np.array_equal(got, a)  # all keys equal: input order
