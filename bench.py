@@ -17,9 +17,16 @@ one step's copy out overlaps the next step's copy in, with the latency of one
 blocking call beside it (``single_call_ms``);
 ``roofline`` is the dominant kernel's algorithmic bytes over its measured
 launch time against the measured HBM copy bandwidth; ``cpu_baseline`` is the
-CPU oracle timed on a bounded sample on this host.  With N > 1 (torchrun)
-every rank sorts its own replica of the workload ("replicas only": the sort
-has no exchange step) and rank 0 reports the max-over-ranks time.
+CPU oracle timed on this host (single-threaded on a bounded sample, and on
+every core over the whole workload).  The line also carries the other
+configurations, each measured in the same process: ``skew`` (the skewed 10 GB
+sort), ``host_modes`` (the 20 GB partially in-memory and the external sort of
+pinned host records under a 30 GB device budget, each output checked
+completely by the oracle), ``batch`` and ``serve`` (many uneven requests,
+batched and through the continuous-batching server, against one launch per
+request).  With N > 1 (torchrun) every rank sorts its own replica of the
+workload ("replicas only": the sort has no exchange step) and rank 0 reports
+the max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -164,16 +171,21 @@ def barrier(pg, device=None):
 
 # ----------------------------------------------------------- CPU baseline
 
-def oracle_sample(n_sample: int, seed: int = 2, skew: bool = False, device=None):
-    """The CPU oracle (single-threaded qsort on (key, index) + record copy) on
-    the first n_sample records of the workload.  Returns (GB/s, seconds)."""
+def oracle_sample(n_sample: int, seed: int = 2, skew: bool = False, device=None,
+                  threads: int = 1):
+    """The CPU oracle on the first n_sample records of the workload: with one
+    thread the qsort on (key, index) + record copy, with more the chunked
+    sort + T-way merge + parallel copy.  Returns (GB/s, seconds)."""
     import datagen
     import oracle
     gen = datagen.skew_records if skew else datagen.uniform_records
     recs = gen(n_sample, seed=seed, device=device or "cpu").cpu().numpy()
     oracle.build()
     t0 = time.perf_counter()
-    oracle.sort_records(recs, key_bytes=KEY)
+    if threads == 1:
+        oracle.sort_records(recs, key_bytes=KEY)
+    else:
+        oracle.sort_records_threads(recs, key_bytes=KEY, threads=threads)
     dt = time.perf_counter() - t0
     return n_sample * REC / dt / 1e9, dt
 
@@ -361,8 +373,20 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         cpu = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {args.cpu_sample} records of the workload, "
                          f"single-threaded qsort + record copy, {dt:.1f} s"}
+        nt = os.cpu_count() or 1
+        nthr = min(n, args.cpu_threads_sample) if args.cpu_threads_sample else n
+        vt, dtt = oracle_sample(nthr, seed=2 if wl == "uniform" else 3, skew=wl == "skew",
+                                device=dev, threads=nt)
+        cpu["threads"] = {
+            "value": round(vt, 4), "unit": "GB/s", "cores": nt, "kind": "oracle",
+            "sample": (f"{'the whole workload' if nthr == n else f'first {nthr} records'}"
+                       f" ({nthr} records), {nt} threads: chunked (key, index) sorts, "
+                       f"T-way merge, parallel record copy, {dtt:.1f} s")}
 
     value = world * n * REC / (ms * 1e-3) / 1e9
+    extras = {}
+    if wl == "uniform" and kb == KEY and world == 1 and not args.quick:
+        extras = run_extras(args, dev, stream, pg, world)
     return {
         "metric": (METRIC if wl == "uniform" and kb == KEY
                    else f"GB/s of 100-byte records sorted ({wl} keys, {kb}-byte key)"),
@@ -375,8 +399,45 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches, "step_ms": step_stats, "e2e": e2e,
         "roofline": roofline,
-        "cpu_baseline": cpu, "kernels": kernels,
+        "cpu_baseline": cpu, "kernels": kernels, **extras,
     }
+
+
+def run_extras(args, dev, stream, pg, world):
+    """The other configurations, measured in the same process after the main
+    workload: the skewed 10 GB sort, the batched and served request streams,
+    and the host-memory modes.  A configuration that fails is reported with
+    its error instead of ending the run."""
+    import copy
+    import torch
+    import paper_1909_08006_gb300 as ley
+    out = {}
+
+    def sub(name, fn):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        ley.ley_release_cache()
+        torch.cuda.empty_cache()
+
+    sub("skew", lambda: run_skew_sub(args, dev, stream, pg))
+    a = copy.copy(args)
+    a.requests, a.steps, a.warmup = 256, 3, 3
+    sub("batch", lambda: _strip(run_batch(a, world, 0, dev, stream, pg)))
+    a = copy.copy(args)
+    a.requests, a.budget_gb = 10_000, 40.0
+    sub("serve", lambda: _strip(run_serve(a, world, 0, dev, stream, pg)))
+    sub("host_modes", lambda: host_modes(args, dev, stream, pg, world))
+    return out
+
+
+def _strip(line):
+    """A configuration's own bench line as a sub-object of the main line."""
+    drop = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data")
+    return {k: v for k, v in line.items() if k not in drop}
 
 
 # ------------------------------------------------------ other workloads
@@ -421,10 +482,32 @@ def run_pairs(args, world, rank, dev, stream, pg):
     }
 
 
+def _check_records_on_oracle(pairs_of_tensors):
+    """Complete oracle check of sorted device outputs against their tagged
+    device inputs ([(in, out)], local index at bytes 10..13): -1 each if exact."""
+    import oracle
+    oracle.build()
+    return [oracle.check_tagged_threads(o.cpu().numpy(), x.cpu().numpy())
+            for x, o in pairs_of_tensors]
+
+
+def _check_pairs_on_oracle(quads):
+    """Complete oracle check of sorted (key, payload) outputs whose payloads
+    are the input positions: -1 each if exact."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    return [oracle.check_pairs_tagged(ko.cpu().numpy().view(np.uint64),
+                                      vo.cpu().numpy().view(np.uint32),
+                                      k.cpu().numpy().view(np.uint64))
+            for k, _v, ko, vo in quads]
+
+
 def run_batch(args, world, rank, dev, stream, pg):
     """Many sort requests of uneven sizes (log-uniform in [lo, hi] records),
     half 100-byte records and half (u64 key, u32 payload) pairs: one batched
-    call per kind against one call per request, same stream, same data."""
+    call per kind against one call per request, same stream, same data.
+    Every request's output is then checked completely by the oracle."""
     import torch
     import datagen
     import paper_1909_08006_gb300 as ley
@@ -433,7 +516,7 @@ def run_batch(args, world, rank, dev, stream, pg):
     rec_reqs, pair_reqs = [], []
     for i, n in enumerate(sizes):
         if i % 2 == 0:
-            x = datagen.uniform_records(n, seed=1000 + i, device=dev)
+            x = datagen.uniform_records(n, seed=1000 + i, device=dev, tag_index=True)
             rec_reqs.append((x, torch.empty_like(x)))
         else:
             k, v = datagen.uniform_pairs(n, seed=1000 + i, device=dev)
@@ -459,6 +542,8 @@ def run_batch(args, world, rank, dev, stream, pg):
     if ley.ley_last_device_status(stream) != ley.LEY_OK:
         raise RuntimeError("device-side error")
     outs_b = [o.clone() for _, o in rec_reqs] + [ko.clone() for _, _, ko, _ in pair_reqs]
+    bad_r = _check_records_on_oracle(rec_reqs)
+    bad_p = _check_pairs_on_oracle(pair_reqs)
     launches0 = ley.ley_launch_count()
     ms_s = _timed(one_by_one, args.steps, args.warmup, stream, pg, dev)
     launches_s = (ley.ley_launch_count() - launches0) // (args.steps + args.warmup)
@@ -479,7 +564,9 @@ def run_batch(args, world, rank, dev, stream, pg):
             "value": round(world * total_bytes / (ms_s * 1e-3) / 1e9, 2), "unit": "GB/s",
             "ms_per_step": round(ms_s, 3), "gpu_launches": launches_s},
         "speedup_vs_one_launch_per_request": round(ms_s / ms_b, 3),
-        "identical_outputs": same,
+        "oracle_checked": len(bad_r) + len(bad_p),
+        "oracle_exact": all(b == -1 for b in bad_r + bad_p),
+        "identical_to_one_launch_per_request": same,
     }
 
 
@@ -490,33 +577,29 @@ def run_serve(args, world, rank, dev, stream, pg):
     gives the capacity, batched and with one request per launch; Poisson
     arrivals at 0.5x and 0.9x of the batched capacity give p50/p99 latency.
     Inputs are resident in HBM: P distinct inputs per kind drawn from the size
-    distribution, each with Q output buffers that requests rotate through."""
+    distribution, each with Q output buffers that requests rotate through.
+    After the saturation run the output buffers of the first rotation slot
+    (the last request that used each) are checked completely by the oracle."""
     import threading
     import numpy as np
     import torch
     import datagen
     import paper_1909_08006_gb300 as ley
     count, lo, hi = args.requests, args.req_min, args.req_max
-    P, Q = args.serve_inputs, 4
+    P, Q = args.serve_inputs, 2
     budget = int(args.budget_gb * 1e9)
     sizes = datagen.log_uniform_sizes(2 * P, seed=11, lo=lo, hi=hi)
-    ins, outs, alone, nbytes = [[], []], [[], []], [[], []], [[], []]
+    ins, outs, nbytes = [[], []], [[], []], [[], []]
     for b in range(P):
         n = sizes[2 * b]
-        x = datagen.uniform_records(n, seed=3000 + b, device=dev)
+        x = datagen.uniform_records(n, seed=3000 + b, device=dev, tag_index=True)
         ins[0].append(x)
         outs[0].append([torch.empty_like(x) for _ in range(Q)])
-        a = torch.empty_like(x)
-        ley.ley_sort_records(x, a)
-        alone[0].append(a)
         nbytes[0].append(n * REC)
         n = sizes[2 * b + 1]
         k, v = datagen.uniform_pairs(n, seed=4000 + b, device=dev)
         ins[1].append((k, v))
         outs[1].append([(torch.empty_like(k), torch.empty_like(v)) for _ in range(Q)])
-        ak, av = torch.empty_like(k), torch.empty_like(v)
-        ley.ley_sort_keys_index(k, v, ak, av)
-        alone[1].append((ak, av))
         nbytes[1].append(n * 12)
     torch.cuda.synchronize()
 
@@ -525,10 +608,10 @@ def run_serve(args, world, rank, dev, stream, pg):
         b = (i // 2) % P
         return kind, b, (i // (2 * P)) % Q
 
-    def serve(max_batch, arrivals):
+    def serve(max_batch, arrivals, latency=True):
         srv = ley.ley_server_create(budget, max_batch=max_batch, slots=args.serve_slots)
         free = {}
-        lat, done_t, bad = [None] * count, [0.0] * count, [0]
+        lat, done_t = [None] * count, [0.0] * count
         tickets = [None] * count
         ready = [threading.Event() for _ in range(count)]
         base = time.perf_counter()
@@ -540,17 +623,10 @@ def run_serve(args, world, rank, dev, stream, pg):
                 late = tickets[i][1]  # submission lateness against the scheduled arrival
                 lat[i] = tm["done_s"] - tm["submit_s"] + late
                 done_t[i] = tm["done_s"]
-                kind, b, q = plan(i)
-                if i % 32 == 0:
-                    o = outs[kind][b][q]
-                    same = torch.equal(o, alone[0][b]) if kind == 0 else (
-                        torch.equal(o[0], alone[1][b][0]) and torch.equal(o[1], alone[1][b][1]))
-                    bad[0] += 0 if same else 1
-                free[(kind, b, q)].set()
+                free[plan(i)].set()
 
         w = threading.Thread(target=waiter)
         w.start()
-        t_first = None
         for i in range(count):
             kind, b, q = plan(i)
             ev = free.get((kind, b, q))
@@ -567,8 +643,6 @@ def run_serve(args, world, rank, dev, stream, pg):
             else:
                 (k, v), (ko, vo) = ins[1][b], outs[1][b][q]
                 t = ley.ley_server_submit_pairs(srv, k, v, ko, vo)
-            if t_first is None:
-                t_first = time.perf_counter()
             tickets[i] = (t, late)
             ready[i].set()
         w.join()
@@ -577,16 +651,22 @@ def run_serve(args, world, rank, dev, stream, pg):
         total = sum(nbytes[plan(i)[0]][plan(i)[1]] for i in range(count))
         arr = np.array(lat)
         makespan = max(done_t)  # seconds since the server's creation (just before base)
-        return {"GBps": round(total / makespan / 1e9, 2), "makespan_s": round(makespan, 4),
-                "req_per_s": round(count / makespan, 1),
-                "p50_ms": round(float(np.percentile(arr, 50)) * 1e3, 3),
-                "p99_ms": round(float(np.percentile(arr, 99)) * 1e3, 3),
-                "batches": st["launched_batches"], "checked": count // 32 + (count % 32 > 0),
-                "mismatches": bad[0], "bytes": total}
+        r = {"GBps": round(total / makespan / 1e9, 2), "makespan_s": round(makespan, 4),
+             "req_per_s": round(count / makespan, 1), "batches": st["launched_batches"],
+             "bytes": total}
+        if latency:
+            r["p50_ms"] = round(float(np.percentile(arr, 50)) * 1e3, 3)
+            r["p99_ms"] = round(float(np.percentile(arr, 99)) * 1e3, 3)
+        return r
 
     zero = [0.0] * count
-    sat = serve(args.serve_batch, zero)
-    single = serve(1, zero)
+    sat = serve(args.serve_batch, zero, latency=False)
+    # the last request that used each first-slot output buffer, against the oracle
+    used = {plan(i)[:2] for i in range(count) if plan(i)[2] == 0}
+    bad_r = _check_records_on_oracle([(ins[0][b], outs[0][b][0]) for kd, b in used if kd == 0])
+    bad_p = _check_pairs_on_oracle([(ins[1][b][0], ins[1][b][1], outs[1][b][0][0],
+                                     outs[1][b][0][1]) for kd, b in used if kd == 1])
+    single = serve(1, zero, latency=False)
     rng = np.random.default_rng(12)
     res = {}
     for frac in (0.5, 0.9):
@@ -601,11 +681,50 @@ def run_serve(args, world, rank, dev, stream, pg):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"serve_{count}x[{lo},{hi}]", "requests": count,
                    "budget_bytes": budget, "max_batch": args.serve_batch,
-                   "slots": args.serve_slots, "distinct_inputs_per_kind": P},
+                   "slots": args.serve_slots, "distinct_inputs_per_kind": P,
+                   "output_buffers_per_input": Q},
         "saturation": sat, "one_launch_per_request": single,
         "speedup_vs_one_launch_per_request": round(single["makespan_s"] / sat["makespan_s"], 3),
+        "oracle_checked": len(bad_r) + len(bad_p),
+        "oracle_exact": all(b == -1 for b in bad_r + bad_p),
         **res,
     }
+
+
+def run_skew_sub(args, dev, stream, pg):
+    """The skewed 10 GB internal sort (1e8 records): device time per sort over
+    the timed steps, the per-kernel split, and a complete oracle check of the
+    output (tagged input)."""
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    n = args.n
+    d_in = datagen.skew_records(n, seed=3, device=dev, tag_index=True)
+    d_out = torch.empty_like(d_in)
+    torch.cuda.synchronize()
+    step = lambda: ley.ley_sort_records(d_in, d_out, n=n, rec_bytes=REC, key_bytes=KEY,  # noqa: E731
+                                        stream=stream)
+    ms = _timed(step, args.sub_steps, 3, stream, pg, dev)
+    if ley.ley_last_device_status(stream) != ley.LEY_OK:
+        raise RuntimeError("device-side error in the skewed sorts")
+    ley.ley_profile_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    prof = ley.ley_profile_read()
+    ley.ley_profile_enable(False)
+    peak, _ = load_peaks()
+    import oracle
+    oracle.build()
+    bad = oracle.check_tagged_threads(d_out.cpu().numpy(), d_in.cpu().numpy())
+    return {"workload": f"skew_{n}", "records": n, "ms_per_step": round(ms, 3),
+            "steps": args.sub_steps, "warmup": 3,
+            "GBps": round(n * REC / (ms * 1e-3) / 1e9, 2),
+            "path_frac_306B": round(PATH_BYTES * n / (ms * 1e-3) / 1e9 / peak, 4),
+            "frac_314B_model": round(314 * n / (ms * 1e-3) / 1e9 / peak, 4),
+            "kernels": {k: {"launches_per_sort": c // 3, "ms_per_sort": round(t / 3, 4)}
+                        for k, (c, t) in prof.items()},
+            "parity": {"exact": bad == -1, "how": "oracle check_tagged over every record"}}
 
 
 def _libcuda():
@@ -667,125 +786,251 @@ def e2e_plan(n, want_streams):
     return 1, max(4096, min(n, ne))
 
 
-def link_peaks(dev, nbytes=2 << 30, reps=3):
-    """Host<->device copy rates of this machine, measured now with the same kind
-    of host memory as the sort's buffers: H2D alone, D2H alone, and both
-    directions at once (GB/s each way)."""
-    import ctypes
-    import torch
-    cu = _libcuda()
-    cu.cuMemcpyHtoDAsync_v2.argtypes = [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t,
-                                        ctypes.c_void_p]
-    cu.cuMemcpyDtoHAsync_v2.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t,
-                                        ctypes.c_void_p]
-    h1, h2 = host_alloc(nbytes), host_alloc(nbytes)
-    d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+class LinkMeter:
+    """Host<->device copy rates of this machine, measured on demand with the same
+    kind of host memory as the sort's buffers (cuMemHostAlloc): H2D alone,
+    D2H alone, and both directions at once (GB/s each way).  The buffers are
+    allocated once, so a reading can be taken right before every timed call:
+    the shared hosts' link rates drift between and within processes."""
 
-    def h2d():
-        assert cu.cuMemcpyHtoDAsync_v2(d1.data_ptr(), h1.ctypes.data, nbytes, s1.cuda_stream) == 0
+    def __init__(self, dev, nbytes=2 << 30):
+        import ctypes
+        import torch
+        self.cu = _libcuda()
+        self.cu.cuMemcpyHtoDAsync_v2.argtypes = [ctypes.c_uint64, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p]
+        self.cu.cuMemcpyDtoHAsync_v2.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
+                                                 ctypes.c_size_t, ctypes.c_void_p]
+        self.dev, self.nbytes = dev, nbytes
+        self.h1, self.h2 = host_alloc(nbytes), host_alloc(nbytes)
+        self.d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.s1, self.s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def d2h():
-        assert cu.cuMemcpyDtoHAsync_v2(h2.ctypes.data, d2.data_ptr(), nbytes, s2.cuda_stream) == 0
+    def measure(self, reps=3):
+        import torch
+        cu, nb = self.cu, self.nbytes
 
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(reps):
+        def h2d():
+            assert cu.cuMemcpyHtoDAsync_v2(self.d1.data_ptr(), self.h1.ctypes.data, nb,
+                                           self.s1.cuda_stream) == 0
+
+        def d2h():
+            assert cu.cuMemcpyDtoHAsync_v2(self.h2.ctypes.data, self.d2.data_ptr(), nb,
+                                           self.s2.cuda_stream) == 0
+
+        def timed(fn):
             fn()
-        torch.cuda.synchronize(dev)
-        return (time.perf_counter() - t0) / reps
+            torch.cuda.synchronize(self.dev)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize(self.dev)
+            return (time.perf_counter() - t0) / reps
 
-    r = {"h2d_GBps": nbytes / timed(h2d) / 1e9, "d2h_GBps": nbytes / timed(d2h) / 1e9,
-         "duplex_each_GBps": nbytes / timed(lambda: (h2d(), d2h())) / 1e9}
-    del d1, d2
-    host_free(h1)
-    host_free(h2)
-    return {k: round(v, 1) for k, v in r.items()}
+        r = {"h2d_GBps": nb / timed(h2d) / 1e9, "d2h_GBps": nb / timed(d2h) / 1e9,
+             "duplex_each_GBps": nb / timed(lambda: (h2d(), d2h())) / 1e9}
+        return {k: round(v, 1) for k, v in r.items()}
+
+    def close(self):
+        host_free(self.h1)
+        host_free(self.h2)
+        del self.d1, self.d2
+
+
+def link_peaks(dev, nbytes=2 << 30, reps=3):
+    """One reading of the link with buffers of its own (see LinkMeter)."""
+    m = LinkMeter(dev, nbytes)
+    try:
+        return m.measure(reps)
+    finally:
+        m.close()
+
+
+def host_avail_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, meter=None,
+                  check=True):
+    """One host-memory configuration: n tagged uniform 100-byte records in
+    pinned host memory, sorted host to host under the device budget (the
+    partially in-memory sort or the external sort, whichever the library
+    picks for that budget), timed over `calls` calls after `warm` warm-ups,
+    each call preceded by a reading of the link.  The output of the last call
+    is then checked completely by the oracle (permutation by tags, bytes, and
+    strict (key, index) order) and at sampled ranks from the definition."""
+    import numpy as np
+    import torch
+    import datagen
+    import paper_1909_08006_gb300 as ley
+    own_meter = meter is None
+    if own_meter:
+        meter = LinkMeter(dev)
+    h_in_np, h_out_np = host_alloc(n * REC), host_alloc(n * REC)
+    try:
+        h_in = torch.from_numpy(h_in_np).view(n, REC)
+        h_out = torch.from_numpy(h_out_np).view(n, REC)
+        chunk = 50_000_000
+        for c0 in range(0, n, chunk):
+            c1 = min(n, c0 + chunk)
+            h_in[c0:c1].copy_(datagen.uniform_records(c1 - c0, seed=2, device=dev, start=c0,
+                                                      tag_index=True).cpu())
+        torch.cuda.synchronize()
+        ws = ley.ley_workspace_bytes(n, mem_budget=budget)
+        picked = "partial" if ws >= n * REC else "external"
+        for _ in range(warm):
+            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
+                                 mem_budget=budget, stream=stream)
+        times, links = [], []
+        for _ in range(calls):
+            links.append(meter.measure())
+            barrier(pg, dev)
+            t0 = time.perf_counter()
+            ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
+                                 mem_budget=budget, stream=stream)
+            times.append(max_over_ranks(time.perf_counter() - t0, pg, dev))
+        link_after = meter.measure()
+        if ley.ley_last_device_status(stream) != ley.LEY_OK:
+            raise RuntimeError("device-side error in the host-mode sorts")
+        parity = None
+        if check:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            bad = oracle.check_tagged_threads(h_out_np.reshape(n, REC), h_in_np.reshape(n, REC))
+            samples = np.linspace(0, n - 1, 4).astype(np.uint64)
+            ranks = oracle.rank_records(h_in_np.reshape(n, REC), samples)
+            out2 = h_out_np.reshape(n, REC)
+            in2 = h_in_np.reshape(n, REC)
+            ranks_ok = all(np.array_equal(out2[int(r)], in2[int(s_)])
+                           for r, s_ in zip(ranks, samples))
+            parity = {"exact": bool(bad == -1 and ranks_ok), "complete_check_first_bad": bad,
+                      "sampled_ranks": int(len(samples)), "sampled_ranks_ok": bool(ranks_ok),
+                      "check_s": round(time.perf_counter() - t0, 1),
+                      "how": "oracle check_tagged over every output record (tags at bytes "
+                             "10..13: permutation, bytes equal the input, strict (key, index) "
+                             "order) + oracle rank_records at 4 sampled inputs"}
+    finally:
+        host_free(h_in_np)
+        host_free(h_out_np)
+        if own_meter:
+            meter.close()
+    link_b = 2 * n * REC if picked == "partial" else 4 * n * REC
+    per_call = []
+    for dt, lk in zip(times, links):
+        # partial: the copy out waits for the finished order, so the floor is
+        # the serial n*100/h2d + n*100/d2h; external: runs in and out, then
+        # partitions in and out (2 n*100 bytes each way) with both directions
+        # overlapped, so the floor is 2 n*100 / duplex rate each way
+        serial = n * REC / (lk["h2d_GBps"] * 1e9) + n * REC / (lk["d2h_GBps"] * 1e9)
+        if picked == "external":
+            serial *= 2
+        duplex = 2 * n * REC / (lk["duplex_each_GBps"] * 1e9)
+        floor = serial if picked == "partial" else duplex
+        per_call.append({"s": round(dt, 4), "floor_s": round(floor, 4),
+                         "frac": round(floor / dt, 4),
+                         "frac_serial_floor": round(serial / dt, 4), "link": lk})
+    med = statistics.median(times)
+    fr = [c["frac"] for c in per_call]
+    return {
+        "mode": picked, "records": n, "bytes": n * REC, "budget_bytes": budget,
+        "device_bytes": ws, "calls": calls, "warmup": warm,
+        "median_s": round(med, 4), "min_s": round(min(times), 4), "max_s": round(max(times), 4),
+        "GBps": round(world * n * REC / med / 1e9, 2),
+        "link_GBps": round(link_b / med / 1e9, 2),
+        "frac_median": round(statistics.median(fr), 4), "frac_min": min(fr), "frac_max": max(fr),
+        "floor": ("serial: n*100/h2d + n*100/d2h" if picked == "partial"
+                  else "duplex: 2*n*100 / (rate each way with both directions busy)"),
+        "per_call": per_call, "link_after": link_after, "parity": parity,
+    }
 
 
 def run_host_mode(args, world, rank, dev, stream, pg):
     """Records in pinned host memory, sorted to pinned host memory under a
     device budget: the partially in-memory sort (input resident on the device)
     or the external sort (runs + k-way merge)."""
-    import torch
-    import datagen
-    import paper_1909_08006_gb300 as ley
-    import numpy as np
     n, budget = args.n, int(args.budget_gb * 1e9)
-    h_in_np, h_out_np = host_alloc(n * REC), host_alloc(n * REC)
-    h_in = torch.from_numpy(h_in_np).view(n, REC)
-    h_out = torch.from_numpy(h_out_np).view(n, REC)
-    chunk = 50_000_000
-    for c0 in range(0, n, chunk):
-        c1 = min(n, c0 + chunk)
-        h_in[c0:c1].copy_(datagen.uniform_records(c1 - c0, seed=2, device=dev, start=c0).cpu())
-    steps, warm = max(1, args.steps), max(1, min(args.warmup, 1))
-    for _ in range(warm):
-        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, mem_budget=budget,
-                             stream=stream)
-    barrier(pg, dev)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY, mem_budget=budget,
-                             stream=stream)
-    dt = max_over_ranks((time.perf_counter() - t0) / steps, pg, dev)
-    ws = ley.ley_workspace_bytes(n)
-    mode = "partial" if n * REC + ws <= budget else "external"
-    del h_in, h_out
-    host_free(h_in_np)
-    host_free(h_out_np)
-    link = 2 * n * REC if mode == "partial" else 4 * n * REC
-    lp = link_peaks(dev)
-    if mode == "partial":
-        # the copy in and the copy out cannot overlap (the gather needs the
-        # finished order): floor = n*100/h2d + n*100/d2h
-        floor_s = n * REC / (lp["h2d_GBps"] * 1e9) + n * REC / (lp["d2h_GBps"] * 1e9)
-        roof = {"bound": "link", "achieved": round(link / dt / 1e9, 1),
-                "peak": round(link / floor_s / 1e9, 1), "unit": "GB/s",
-                "frac": round(floor_s / dt, 4), "peak_source": "measured in this run (serial H2D + D2H)"}
-    else:
-        # runs in and out, then partitions in and out: 2*n*100 bytes each
-        # way, the two directions overlapped
-        each = 2 * n * REC / dt / 1e9
-        roof = {"bound": "link", "achieved": round(each, 1), "peak": lp["duplex_each_GBps"],
-                "unit": "GB/s each way", "frac": round(each / lp["duplex_each_GBps"], 4),
-                "peak_source": "measured in this run (full duplex)"}
+    r = host_mode_run(args, dev, stream, pg, world, args.workload, n, budget,
+                      calls=max(1, args.steps), warm=max(1, min(args.warmup, 1)),
+                      check=not args.no_check)
+    roof = {"bound": "link", "achieved": r["link_GBps"], "frac": r["frac_median"],
+            "unit": "GB/s", "peak_source": "measured in this run before each call (" +
+            r["floor"] + ")"}
     return {
-        "metric": f"GB/s of 100-byte records sorted host-to-host ({mode}, device budget)",
-        "value": round(world * n * REC / dt / 1e9, 2), "unit": "GB/s", "n_gpus": world,
-        "steps": steps, "warmup": warm, "ms_per_step": round(dt * 1e3, 1),
+        "metric": f"GB/s of 100-byte records sorted host-to-host ({r['mode']}, device budget)",
+        "value": r["GBps"], "unit": "GB/s", "n_gpus": world,
+        "steps": r["calls"], "warmup": r["warmup"], "ms_per_step": round(r["median_s"] * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": {"workload": f"{args.workload}_{n}", "records": n,
-                                        "budget_bytes": budget, "mode": mode,
-                                        "link_bytes_per_step": link},
-        "link_GBps": round(link / dt / 1e9, 2), "roofline": roof, "link_peaks": lp,
+                                        "budget_bytes": budget, "mode": r["mode"]},
+        "roofline": roof, "host_mode": r,
     }
+
+
+def host_modes(args, dev, stream, pg, world):
+    """The 20 GB partially in-memory sort and the external sort, each at the
+    largest size host memory allows up to its configuration (2e8 and 4e8
+    records), under the 30 GB device budget."""
+    import torch
+    import paper_1909_08006_gb300 as ley
+    budget = int(30e9)
+    out = {}
+    meter = LinkMeter(dev)
+    try:
+        for mode, want, per_rec in (("partial", 200_000_000, 2 * REC),
+                                    ("external", 400_000_000, 3 * REC)):
+            avail = host_avail_bytes()
+            n = want
+            if avail is not None:  # input, output (and the run scratch) pinned on the host
+                share = 0.7 * avail / int(os.environ.get("LOCAL_WORLD_SIZE", "1")) - (8 << 30)
+                n = max(4096, min(want, int(share // per_rec) // 4096 * 4096))
+            try:
+                out[mode] = host_mode_run(args, dev, stream, pg, world, mode, n, budget,
+                                          calls=args.host_calls, warm=1, meter=meter)
+                if n < want:
+                    out[mode]["note"] = (f"{n} of {want} records: host memory "
+                                         f"({avail} bytes available) limits the pinned buffers")
+            except Exception as e:  # noqa: BLE001 - reported in the line
+                out[mode] = {"error": f"{type(e).__name__}: {e}"}
+            ley.ley_release_cache()
+            torch.cuda.empty_cache()
+    finally:
+        meter.close()
+    return out
 
 
 # ------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank, pg):
     """The oracle, as it stands, on the host cores: each step sorts a bounded
-    sample of the same workload (the paper's system is CPU code with no GPU
-    path; the oracle is this project's CPU statement of the same sort)."""
+    sample of the same workload on every core (the paper's system is CPU code
+    with no GPU path; the oracle is this project's CPU statement of the same
+    sort, here in its multi-core form: chunked (key, index) sorts, a T-way
+    merge and a parallel record copy)."""
     if rank != 0:
         return None
     import datagen
     import oracle
     oracle.build()
+    threads = os.cpu_count() or 1
     recs = datagen.uniform_records(args.ref_sample, seed=2).numpy()
     for _ in range(args.warmup):
-        oracle.sort_records(recs, key_bytes=KEY)
+        oracle.sort_records_threads(recs, key_bytes=KEY, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sort_records(recs, key_bytes=KEY)
+        oracle.sort_records_threads(recs, key_bytes=KEY, threads=threads)
     dt = (time.perf_counter() - t0) / args.steps
     v = args.ref_sample * REC / dt / 1e9
-    sample = (f"first {args.ref_sample} records of the workload per step, "
-              "single-threaded qsort on (key, index) + record copy")
+    sample = (f"first {args.ref_sample} records of the workload per step, {threads} threads: "
+              "chunked qsort on (key, index), T-way merge, parallel record copy")
     return {
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -793,8 +1038,8 @@ def run_reference(args, world, rank, pg):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"uniform_{args.n}", "records": args.n, "record_bytes": REC,
                    "key_bytes": KEY},
-        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -823,12 +1068,23 @@ def main():
                     help="run the library's autotuner on the workload's size first")
     ap.add_argument("--serve-batch", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=3)
-    ap.add_argument("--serve-inputs", type=int, default=64)
+    ap.add_argument("--serve-inputs", type=int, default=256)
     ap.add_argument("--requests", type=int, default=None)
     ap.add_argument("--req-min", type=int, default=1000)
     ap.add_argument("--req-max", type=int, default=10_000_000)
     ap.add_argument("--budget-gb", type=float, default=30.0)
-    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=10_000_000,
+                    help="records per step of the reference arm (the oracle on every core)")
+    ap.add_argument("--cpu-threads-sample", type=int, default=0,
+                    help="records of the multi-core oracle baseline (0 = the whole workload)")
+    ap.add_argument("--host-calls", type=int, default=3,
+                    help="timed calls per host-memory mode in the default line")
+    ap.add_argument("--sub-steps", type=int, default=10,
+                    help="timed steps of the skewed sort in the default line")
+    ap.add_argument("--quick", action="store_true",
+                    help="the main workload only (no skew, batch, serve or host-mode entries)")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the oracle check of a --workload partial/external run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "external" and args.n == 100_000_000:

@@ -69,7 +69,9 @@ typedef void* ley_stream_t;
  *               external run-formation + k-way merge sort; these block until
  *               the sorted records are in `out`.  Any other combination
  *               (mixed, pageable host memory) is LEY_EINVAL.
- *   rec_bytes   4..4096, a multiple of 4 (100 takes the specialised kernels).
+ *   rec_bytes   key_bytes..4096, any size (100 takes the specialised kernels;
+ *               sizes that are a multiple of 4 are gathered in words, others
+ *               in bytes).
  *   key_bytes   1..rec_bytes; the key is at offset 0.  A (key, pointer) tuple
  *               holds 12 key bytes, so a longer key is sorted one 12-byte
  *               window at a time, least significant window first
@@ -171,18 +173,27 @@ ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t cou
  * its own ley_sort_records / ley_sort_keys_index call would sort it.
  *
  * Submission checks the request's arguments like the single-request call
- * (a rejected request gets no ticket).  ley_server_wait blocks until the request is done, returns its status (as
- * ley_last_device_status would report it for the batch that carried it) and
- * its submit / launch / completion times in seconds since the server was
- * created; a ticket can be waited for once.  ley_server_destroy finishes all
- * submitted work, then stops the server's threads.
+ * (a rejected request gets no ticket).  ley_server_wait blocks until the
+ * request is done, returns its status (as ley_last_device_status would report
+ * it for the batch that carried it), its submit / launch / completion times
+ * on the host clock in seconds since the server was created, and its batch's
+ * interval on the device clock; a ticket can be waited for once.
+ * ley_server_destroy finishes all submitted work, then stops the server's
+ * threads.
  */
 typedef struct ley_server ley_server;
 
 typedef struct {
-    double submit_s;  /* submission */
-    double start_s;   /* its batch was launched */
-    double done_s;    /* its batch's completion was observed on the host */
+    double submit_s;     /* submission (host clock) */
+    double start_s;      /* its batch was launched (host clock) */
+    double done_s;       /* its batch's completion was observed on the host */
+    double dev_start_s;  /* device clock, seconds after an event recorded at server
+                            creation: a timing event on the batch's launch stream
+                            just before its first kernel, i.e. when the stream
+                            reached the batch's work */
+    double dev_done_s;   /* device clock: the event after the batch's last kernel
+                            (negative if the batch could not be timed) */
+    uint64_t batch;      /* the batch that carried the request: 1, 2, ... in launch order */
 } ley_server_times;
 
 typedef struct {
@@ -258,11 +269,24 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
                              uint32_t rec_bytes, uint32_t key_bytes, ley_stream_t stream);
 
 /*
- * Device scratch (bytes) that ley_sort_records would allocate for an internal
- * sort of n records of this geometry.  Host-only; needs no GPU.
+ * Device scratch (bytes) that ley_sort_records allocates for n records of
+ * this geometry (Sections 1 and 4.1: a data set sorted under a memory limit),
+ * so that a caller can size a sort before making it.  Host-only; needs no GPU.
+ *   mem_budget == 0  the internal sort of device buffers.  (With device
+ *                    buffers and a budget, the internal sort allocates the
+ *                    same bytes and returns LEY_ENOMEM when they exceed the
+ *                    budget.)
+ *   mem_budget > 0   the sort of pinned host buffers under that budget: the
+ *                    partially in-memory mode's device bytes (the resident
+ *                    input, the workspace, the staging buffers) when they fit,
+ *                    else the external mode's (its rotating run buffers,
+ *                    workspaces and staging); LEY_ENOMEM, with *bytes = 0,
+ *                    when neither fits.  The external mode's pinned host
+ *                    scratch (n * rec_bytes bytes, the sorted runs) is host
+ *                    memory and not counted.
  */
 ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
-                               uint64_t* bytes);
+                               uint64_t mem_budget, uint64_t* bytes);
 
 /*
  * Returns the memory this library keeps between calls: the unused part of
@@ -277,9 +301,9 @@ ley_status ley_release_cache(void);
  * result; they decide which path a bucket takes (the bigBucketThreshold and
  * tinyBucketThreshold of Section 3.1, Algorithm 1, which the paper leaves
  * unstated) and how many CTAs per SM the finishing and scatter kernels run.
- * They apply to sorts started after ley_set_tuning returns (set them when no
- * other thread is starting sorts).  The allocation-free entry point always
- * uses the defaults.
+ * They apply to sorts started after ley_set_tuning returns; a sort already
+ * started keeps the tuning it read when it started.  The allocation-free
+ * entry point always uses the defaults.
  */
 typedef struct {
     uint32_t big_bucket;          /* buckets above this many tuples are scattered again;
@@ -310,10 +334,18 @@ ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_byt
  * rec_bytes on the device (16-byte aligned), read and never written; the
  * timed sorts go to scratch of n * rec_bytes bytes.  Thresholds that suit
  * one key distribution (say uniform) can be slower on another (say skewed),
- * so tuning on the data to be sorted is the reliable form.  Blocks.
+ * so tuning on the data to be sorted is the reliable form.  The timed sorts
+ * run on a stream of the library's own that first waits for the work queued
+ * on `stream` before the call (the work that may still be writing `in`).
+ * Blocks.
+ *
+ * Both autotuners time every candidate as that sort's own tuning and make
+ * the winner current only when they return: sorts started by other threads
+ * meanwhile keep the tuning that was current before.  Every sort reads the
+ * current tuning once, when it starts, and uses that copy throughout.
  */
 ley_status ley_autotune_records_on(const void* in, uint64_t n, uint32_t rec_bytes,
-                                   uint32_t key_bytes, ley_tuning* best);
+                                   uint32_t key_bytes, ley_tuning* best, ley_stream_t stream);
 
 /* Static English text for a status code (never NULL). */
 const char* ley_status_string(ley_status s);

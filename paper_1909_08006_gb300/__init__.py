@@ -64,7 +64,8 @@ class _Tuning(ctypes.Structure):
 
 class _ServerTimes(ctypes.Structure):
     _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
-                ("done_s", ctypes.c_double)]
+                ("done_s", ctypes.c_double), ("dev_start_s", ctypes.c_double),
+                ("dev_done_s", ctypes.c_double), ("batch", ctypes.c_uint64)]
 
 
 class _ServerCounters(ctypes.Structure):
@@ -74,8 +75,8 @@ class _ServerCounters(ctypes.Structure):
 
 def library_path() -> str:
     """The library this binding loads: the in-tree build, or the file named by
-    the LEYSORT_LIB environment variable (an alternative build of the same
-    sources, e.g. one with kernel phase timers)."""
+    the LEYSORT_LIB environment variable (another build of the same
+    sources)."""
     return os.environ.get("LEYSORT_LIB") or _build.LIB
 
 
@@ -98,7 +99,7 @@ def _load() -> ctypes.CDLL:
     lib.ley_sort_keys_index.restype = ctypes.c_int
     lib.ley_partition_records.argtypes = [vp, u64, u32, u32, u32, vp, vp, vp]
     lib.ley_partition_records.restype = ctypes.c_int
-    lib.ley_workspace_bytes.argtypes = [u64, u32, u32, ctypes.POINTER(u64)]
+    lib.ley_workspace_bytes.argtypes = [u64, u32, u32, u64, ctypes.POINTER(u64)]
     lib.ley_workspace_bytes.restype = ctypes.c_int
     lib.ley_status_string.argtypes = [ctypes.c_int]
     lib.ley_status_string.restype = ctypes.c_char_p
@@ -128,7 +129,7 @@ def _load() -> ctypes.CDLL:
     lib.ley_set_tuning.restype = ctypes.c_int
     lib.ley_autotune_records.argtypes = [u64, u32, u32, u64, ctypes.POINTER(_Tuning)]
     lib.ley_autotune_records.restype = ctypes.c_int
-    lib.ley_autotune_records_on.argtypes = [vp, u64, u32, u32, ctypes.POINTER(_Tuning)]
+    lib.ley_autotune_records_on.argtypes = [vp, u64, u32, u32, ctypes.POINTER(_Tuning), vp]
     lib.ley_autotune_records_on.restype = ctypes.c_int
     lib.ley_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
     lib.ley_server_create.restype = ctypes.c_int
@@ -318,15 +319,17 @@ def ley_autotune_records(n: int, rec_bytes: int = 100, key_bytes: int = 10,
 
 
 def ley_autotune_records_on(inp, n: int | None = None, rec_bytes: int | None = None,
-                            key_bytes: int = 10) -> dict:
+                            key_bytes: int = 10, stream=None) -> dict:
     """Times a grid of tunings on the caller's device records (a uint8
-    [n, rec_bytes] tensor, not modified); keeps and returns the fastest."""
+    [n, rec_bytes] tensor, not modified) after the work queued on ``stream``
+    (default: the tensor's current stream); keeps and returns the fastest."""
     if n is None:
         n = int(inp.shape[0])
     if rec_bytes is None:
         rec_bytes = int(inp.shape[1]) if hasattr(inp, "shape") and len(inp.shape) == 2 else 100
     t = _Tuning()
-    _check(_lib.ley_autotune_records_on(_addr(inp), n, rec_bytes, key_bytes, ctypes.byref(t)),
+    _check(_lib.ley_autotune_records_on(_addr(inp), n, rec_bytes, key_bytes, ctypes.byref(t),
+                                        _stream(stream, inp)),
            "ley_autotune_records_on")
     return {f: int(getattr(t, f)) for f, _ in _Tuning._fields_}
 
@@ -366,10 +369,11 @@ def ley_server_submit_pairs(server: int, keys_in, idx_in, keys_out, idx_out,
 
 def ley_server_wait(server: int, ticket: int) -> dict:
     """Blocks until the request is done; raises LeyError on a failed request.
-    Returns its submit / start / done times (seconds since server creation)."""
+    Returns its submit / start / done times (host clock, seconds since server
+    creation), its batch's device-clock interval and the batch number."""
     tm = _ServerTimes()
     _check(_lib.ley_server_wait(server, ticket, ctypes.byref(tm)), "ley_server_wait")
-    return {"submit_s": tm.submit_s, "start_s": tm.start_s, "done_s": tm.done_s}
+    return {f: getattr(tm, f) for f, _ in _ServerTimes._fields_}
 
 
 def ley_server_stats(server: int) -> dict:
@@ -438,9 +442,12 @@ def ley_merge_records(runs, run_start, out, rec_bytes: int | None = None, key_by
     return _check(st, "ley_merge_records")
 
 
-def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10) -> int:
+def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10,
+                        mem_budget: int = 0) -> int:
+    """Device bytes a sort of n records allocates: the internal sort's
+    scratch (mem_budget 0), or a host-memory sort's under that budget."""
     v = ctypes.c_uint64(0)
-    _check(_lib.ley_workspace_bytes(n, rec_bytes, key_bytes, ctypes.byref(v)),
+    _check(_lib.ley_workspace_bytes(n, rec_bytes, key_bytes, mem_budget, ctypes.byref(v)),
            "ley_workspace_bytes")
     return int(v.value)
 

@@ -199,7 +199,9 @@ struct Layout {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static Layout make_layout(ull n, bool with_perm, uint32_t big = cur_tuning().big) {
+// Scratch layout of one internal sort of n tuples; `big` (the big-bucket
+// threshold of the sort's tuning) bounds the segment and task counts.
+static Layout make_layout(ull n, bool with_perm, uint32_t big) {
     Layout L{};
     L.cap_seg = n / big + 2;
     L.cap_tiles = n / kPassTile + L.cap_seg + 1;
@@ -258,7 +260,7 @@ static Work make_work(char* base, const Layout& L, ull n, uint32_t* err) {
     return w;
 }
 
-static KeySpec record_keyspec(uint32_t kb, const Tuning& t = cur_tuning()) {
+static KeySpec record_keyspec(uint32_t kb, const Tuning& t) {
     KeySpec ks;
     ks.big = t.big;
     ks.tiny = t.tiny;
@@ -268,7 +270,7 @@ static KeySpec record_keyspec(uint32_t kb, const Tuning& t = cur_tuning()) {
     return ks;
 }
 
-static KeySpec pair_keyspec(const Tuning& t = cur_tuning()) {
+static KeySpec pair_keyspec(const Tuning& t) {
     KeySpec ks;
     ks.big = t.big;
     ks.tiny = t.tiny;
@@ -280,11 +282,12 @@ static KeySpec pair_keyspec(const Tuning& t = cur_tuning()) {
 
 // Record gather for 100-byte records: by default the internal sort gathers
 // the records inside the finishing kernel (2); the separate gather kernel
-// with TMA bulk copies (1, LEY_GATHER=tma) serves the chunked host-memory
-// modes; plain vector loads (0, LEY_GATHER=lsu) are kept for comparison.
+// with TMA bulk copies (1) serves the chunked host-memory modes, and
+// LEY_GATHER=tma makes the internal sort use it too (a test of that kernel
+// on the internal path).  Records read from host memory take the plain-load
+// kernel (0), see stage_gather.
 static int gather_variant() {
     const char* v = std::getenv("LEY_GATHER");
-    if (v && std::strcmp(v, "lsu") == 0) return 0;
     if (v && std::strcmp(v, "tma") == 0) return 1;
     return 2;
 }
@@ -310,6 +313,10 @@ struct SortArgs {
     ull n;
     uint32_t rec, kb, digit;
     bool in_host = false;     // records at `in` are pinned host memory mapped for the device
+    // The tuning of this call, read once when the call starts: every layout,
+    // key spec and grid of the call is sized from this copy, so a concurrent
+    // ley_set_tuning (or the autotuner) cannot change it half-way.
+    Tuning tune;
 };
 
 #define LEY_TRY(x)                                   \
@@ -348,11 +355,14 @@ static int tuned_grid(int sms, KernelKind k, uint32_t want) {
     if (want && (int)want < b) b = (int)want;
     return sms * b;
 }
-static int pass_grid(int sms) { return tuned_grid(sms, KK_PASS, cur_tuning().pass_ctas); }
-static int fin_grid(int sms, KernelKind k) { return tuned_grid(sms, k, cur_tuning().fin_ctas); }
+static int pass_grid(int sms, const Tuning& t) { return tuned_grid(sms, KK_PASS, t.pass_ctas); }
+static int fin_grid(int sms, KernelKind k, const Tuning& t) {
+    return tuned_grid(sms, k, t.fin_ctas);
+}
 
-static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st, int sms) {
-    const LaunchCfg cp{pass_grid(sms), kPassThreads, kernel_smem(KK_PASS), st};
+static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st, int sms,
+                               const Tuning& t) {
+    const LaunchCfg cp{pass_grid(sms, t), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
     const LaunchCfg cc{2 * sms, 128, 0, st};
@@ -367,10 +377,10 @@ static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st
 
 static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const KeySpec& ks,
                                       cudaStream_t st, int sms, bool fuse = false) {
-    ley_status s0 = stage_levels(w, ks, st, sms);
+    ley_status s0 = stage_levels(w, ks, st, sms, a.tune);
     if (s0 != LEY_OK) return s0;
     if (a.mode == MODE_PAIRS) {
-        LaunchCfg cf{fin_grid(sms, KK_FINISH_PAIRS), kFinThreads,
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_PAIRS, a.tune), kFinThreads,
                      kernel_smem(KK_FINISH_PAIRS), st};
         LEY_TRY(launch("finish", st, [&] {
             return launch_finish_pairs(cf, w, ks, a.keys_out, a.idx_out);
@@ -378,14 +388,15 @@ static ley_status stage_levels_finish(const SortArgs& a, const Work& w, const Ke
         return LEY_OK;
     }
     if (fuse) {  // records gathered into a.out by the finishing kernel itself
-        LaunchCfg cf{fin_grid(sms, KK_FINISH_GATHER), kFinThreads,
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_GATHER, a.tune), kFinThreads,
                      kernel_smem(KK_FINISH_GATHER), st};
         LEY_TRY(launch("finish_gather", st, [&] {
             return launch_finish_gather(cf, w, ks, a.in, a.out, a.n);
         }));
         return LEY_OK;
     }
-    LaunchCfg cf{fin_grid(sms, KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+    LaunchCfg cf{fin_grid(sms, KK_FINISH_REC, a.tune), kFinThreads, kernel_smem(KK_FINISH_REC),
+                 st};
     LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
     return LEY_OK;
 }
@@ -396,7 +407,7 @@ static ley_status stage_gather(const SortArgs& a, const uint32_t* perm, cudaStre
     if (j1 <= j0) return LEY_OK;
     // Records read from host memory (over the host link) take the plain-load
     // kernel: bulk copies are only used on device memory.
-    const int gv = a.rec == 100 && !a.in_host ? (gather_variant() == 0 ? 0 : 1) : 0;
+    const int gv = a.rec == 100 && !a.in_host ? 1 : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
@@ -410,7 +421,7 @@ static ley_status stage_gather(const SortArgs& a, const uint32_t* perm, cudaStre
 static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, cudaStream_t st,
                                DevState* ds) {
     Work w = make_work(base, L, a.n, ds->err);
-    const KeySpec ks = a.mode == MODE_PAIRS ? pair_keyspec() : record_keyspec(a.kb);
+    const KeySpec ks = a.mode == MODE_PAIRS ? pair_keyspec(a.tune) : record_keyspec(a.kb, a.tune);
     const int sms = ds->sms;
     const int digit0 = a.mode == MODE_PARTITION ? (int)a.digit : 0;
     ley_status s = stage_prepare(w, L, st, a.n, digit0);
@@ -425,7 +436,7 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
         if (s != LEY_OK) return s;
     }
     if (a.mode == MODE_PARTITION) {
-        const LaunchCfg cp{pass_grid(sms), kPassThreads, kernel_smem(KK_PASS), st};
+        const LaunchCfg cp{pass_grid(sms, a.tune), kPassThreads, kernel_smem(KK_PASS), st};
         const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
         LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, 0); }));
         LEY_TRY(launch("classify", st, [&] { return launch_classify_partition(st, w); }));
@@ -446,12 +457,13 @@ static ley_status enqueue_sort(const SortArgs& a, char* base, const Layout& L, c
 // Sorts the requests of a batch (non-empty, offsets assigned, npos = end of
 // the last request's tiles) as one sort over R top-level segments.
 static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_t rec,
-                            uint32_t kb, bool pairs, ull budget, cudaStream_t st) {
+                            uint32_t kb, bool pairs, ull budget, cudaStream_t st,
+                            const Tuning& tune) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     const uint32_t R = (uint32_t)reqs.size();
     const bool fuse = !pairs && rec == 100;
-    const Layout L = make_layout(npos, !pairs && !fuse);
+    const Layout L = make_layout(npos, !pairs && !fuse, tune.big);
     const uint32_t ntiles = (uint32_t)(npos / kPassTile);
     const size_t rq_bytes = align_up(R * sizeof(BatchReq), 256);
     const size_t tr_bytes = align_up((size_t)ntiles * sizeof(uint32_t), 256);
@@ -464,7 +476,7 @@ static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_
     Work w = make_work(b, L, npos, ds->err);
     BatchReq* dreqs = reinterpret_cast<BatchReq*>(b + L.total);
     uint32_t* tile_req = reinterpret_cast<uint32_t*>(b + L.total + rq_bytes);
-    const KeySpec ks = pairs ? pair_keyspec() : record_keyspec(kb);
+    const KeySpec ks = pairs ? pair_keyspec(tune) : record_keyspec(kb, tune);
     const int sms = ds->sms;
     ley_status s = LEY_OK;
     auto run = [&]() -> ley_status {
@@ -481,17 +493,18 @@ static ley_status run_batch(const std::vector<BatchReq>& reqs, ull npos, uint32_
             return pairs ? launch_batch_extract_pairs(c, dreqs, tile_req, ntiles, w)
                          : launch_batch_extract_records(c, dreqs, tile_req, ntiles, rec, ks, w);
         }));
-        t = stage_levels(w, ks, st, sms);
+        t = stage_levels(w, ks, st, sms, tune);
         if (t != LEY_OK) return t;
         if (pairs || fuse) {
             const KernelKind fk = pairs ? KK_FINISH_PAIRS : KK_FINISH_GATHER;
-            LaunchCfg cf{fin_grid(sms, fk), kFinThreads, kernel_smem(fk), st};
+            LaunchCfg cf{fin_grid(sms, fk, tune), kFinThreads, kernel_smem(fk), st};
             LEY_TRY(launch("finish_gather", st, [&] {
                 return launch_batch_finish(cf, w, ks, dreqs, tile_req, pairs);
             }));
             return LEY_OK;
         }
-        LaunchCfg cf{fin_grid(sms, KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
+        LaunchCfg cf{fin_grid(sms, KK_FINISH_REC, tune), kFinThreads, kernel_smem(KK_FINISH_REC),
+                     st};
         LEY_TRY(launch("finish", st, [&] { return launch_finish_records(cf, w, ks); }));
         LEY_TRY(launch("gather", st, [&] {
             return launch_batch_gather_generic(st, sms * blocks_per_sm(KK_GATHER_GENERIC), dreqs,
@@ -523,7 +536,7 @@ static ley_status enqueue_long_key_order(const SortArgs& a, const Work& w, const
     for (int i = (int)W - 1; i >= 0; i--) {
         const uint32_t koff = kWindow * (uint32_t)i;
         const uint32_t wl = std::min(kWindow, a.kb - koff);
-        const KeySpec ks = record_keyspec(wl);
+        const KeySpec ks = record_keyspec(wl, a.tune);
         ley_status s = stage_prepare(w, L, st, a.n, 0);
         if (s != LEY_OK) return s;
         LaunchCfg c{sms * blocks_per_sm(KK_EXTRACT_REC), 256, 0, st};
@@ -551,7 +564,7 @@ static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     if (a.mode == MODE_RECORDS && a.kb > kWindow) {
-        const Layout L = make_layout(a.n, true);
+        const Layout L = make_layout(a.n, true, a.tune.big);
         const size_t total = L.total + long_key_extra(a.n);
         if (budget && total > budget) return LEY_ENOMEM;
         void* base = nullptr;
@@ -566,7 +579,7 @@ static ley_status run_device_sort(const SortArgs& a, ull budget, cudaStream_t st
         cudaFreeAsync(base, st);
         return s;
     }
-    const Layout L = make_layout(a.n, a.mode == MODE_RECORDS && !fused_gather(a.rec));
+    const Layout L = make_layout(a.n, a.mode == MODE_RECORDS && !fused_gather(a.rec), a.tune.big);
     if (budget && L.total > budget) return LEY_ENOMEM;
     void* base = nullptr;
     if (!scratch_alloc(ds, &base, L.total, st)) return LEY_ENOMEM;
@@ -728,17 +741,26 @@ static ull staging_records(ull n, uint32_t rec, ull budget) {
 // With block false the whole pipeline is only enqueued: every side stream
 // joins `st` before the scratch is freed on it, so work queued on `st` later
 // (or a synchronisation of `st`) comes after the sorted records are in out.
+// Device bytes of the partially in-memory mode: the resident input, one
+// internal sort's workspace (plus the window orders of a long key) and the
+// copy-out staging buffers.
+static size_t partial_need(ull n, uint32_t rec, uint32_t kb, ull budget, const Tuning& t) {
+    const Layout L = make_layout(n, true, t.big);
+    const size_t stg_bytes = align_up(staging_records(n, rec, budget) * rec, 256);
+    return align_up(n * rec, 256) + L.total + kStaging * stg_bytes +
+           (kb > kWindow ? long_key_extra(n) : 0);
+}
+
 static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t st,
                                    bool block = true) {
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     const ull bytes = a.n * a.rec;
-    const Layout L = make_layout(a.n, true);
+    const Layout L = make_layout(a.n, true, a.tune.big);
     const bool long_key = a.kb > kWindow;
     const ull q = staging_records(a.n, a.rec, budget);
     const size_t stg_bytes = align_up(q * a.rec, 256);
-    const size_t need = align_up(bytes, 256) + L.total + kStaging * stg_bytes +
-                        (long_key ? long_key_extra(a.n) : 0);
+    const size_t need = partial_need(a.n, a.rec, a.kb, budget, a.tune);
     if (budget && need > budget) return LEY_ENOMEM;
     void* dmem = nullptr;
     if (!scratch_alloc(ds, &dmem, need, st)) return LEY_ENOMEM;
@@ -754,7 +776,7 @@ static ley_status run_host_partial(const SortArgs& a, ull budget, cudaStream_t s
         SortArgs d = a;
         d.in = reinterpret_cast<const uint8_t*>(din);
         Work w = make_work(ws, L, a.n, ds->err);
-        const KeySpec ks = record_keyspec(a.kb);
+        const KeySpec ks = record_keyspec(a.kb, a.tune);
         hp.mark(hp.h2d, "in begin");
         const uint32_t* order = w.perm;
         if (long_key) {
@@ -911,7 +933,7 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
     SortArgs m = a;
     m.in = dev_runs;
     m.n = off_host[k];
-    const KeySpec ks = record_keyspec(a.kb);
+    const KeySpec ks = record_keyspec(a.kb, a.tune);
     ley_status s = stage_prepare(w, L, st, m.n, 0);
     if (s != LEY_OK) return s;
     s = stage_extract_records(m, w, ks, st, sms, 0, 0, ceil_div_u64(m.n, kPassTile));
@@ -953,26 +975,38 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
 constexpr ull kExtRuns = 16;
 constexpr int kExtBufs = 3;
 constexpr ull kExtMinRun = 4ull << 20;
+constexpr uint32_t kMaxRuns = 128;  // merge fan-in (the offsets travel in kernel parameters)
 
-static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t st) {
-    DevState* ds = dev_state();
-    if (!ds) return LEY_ECUDA;
-    const ull q = staging_records(a.n, a.rec, budget);
-    const size_t stg_bytes = align_up(q * a.rec, 256);
-    const size_t fixed = kStaging * stg_bytes + 64 * 1024;
+// The external mode's device-memory plan under a budget: runs of r_len
+// records (whole tiles, about n / kExtRuns, at most what kExtBufs record
+// buffers and workspaces allow beside the staging buffers), k runs, and the
+// device bytes of the whole pipeline.  LEY_ENOMEM when nothing fits.
+struct ExtPlan {
+    ull q = 0;          // records per staging buffer
+    ull r_len = 0;      // records per run (the largest merge partition too)
+    uint32_t k = 0;     // runs
+    size_t in_bytes = 0, ws_len = 0, stg_bytes = 0, total = 0;
+};
+
+static ley_status external_plan(ull n, uint32_t rec, uint32_t kb, ull budget, const Tuning& t,
+                                ExtPlan* p) {
+    ExtPlan e;
+    e.q = staging_records(n, rec, budget);
+    e.stg_bytes = align_up(e.q * rec, 256);
+    const size_t fixed = kStaging * e.stg_bytes + 64 * 1024;
     if (budget <= fixed) return LEY_ENOMEM;
     // Keys longer than a tuple's 12 bytes: each run, and each merge
     // partition, is sorted window by window (its workspace grows by the two
     // order arrays); the partitions are cut by the same exact co-rank on the
     // whole key, so sorting a partition's slices stably -- ties in slice
     // order, which is (run, position) -- gives its merge.
-    const bool long_key = a.kb > kWindow;
+    const bool long_key = kb > kWindow;
     auto ws_bytes = [&](ull r) {
-        return make_layout(r, true).total + (long_key ? long_key_extra(r) : 0);
+        return make_layout(r, true, t.big).total + (long_key ? long_key_extra(r) : 0);
     };
     // largest run (whole tiles) whose record buffers and workspaces fit
-    auto need = [&](ull r) { return kExtBufs * (align_up(r * a.rec, 256) + ws_bytes(r)) + fixed; };
-    ull lo = 0, hi = a.n / kPassTile + 1;
+    auto need = [&](ull r) { return kExtBufs * (align_up(r * rec, 256) + ws_bytes(r)) + fixed; };
+    ull lo = 0, hi = n / kPassTile + 1;
     while (lo < hi) {
         const ull mid = (lo + hi + 1) / 2;
         if (need(mid * kPassTile) <= budget) lo = mid;
@@ -980,15 +1014,30 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     }
     const ull r_max = lo * kPassTile;
     if (r_max == 0) return LEY_ENOMEM;
-    ull r_len = ceil_div_u64(ceil_div_u64(a.n, kExtRuns), kPassTile) * kPassTile;
-    if (r_len < kExtMinRun) r_len = kExtMinRun;
-    if (r_len > r_max) r_len = r_max;
-    const uint32_t k = (uint32_t)((a.n + r_len - 1) / r_len);
-    if (k > 128) return LEY_ENOMEM;  // budget too small for the merge fan-in
-    const Layout L = make_layout(r_len, true);
-    const size_t in_bytes = align_up(r_len * a.rec, 256);
-    const size_t ws_len = ws_bytes(r_len);
-    const size_t total = kExtBufs * (in_bytes + ws_len) + kStaging * stg_bytes + 8 * 1024;
+    e.r_len = ceil_div_u64(ceil_div_u64(n, kExtRuns), kPassTile) * kPassTile;
+    if (e.r_len < kExtMinRun) e.r_len = kExtMinRun;
+    if (e.r_len > r_max) e.r_len = r_max;
+    e.k = (uint32_t)((n + e.r_len - 1) / e.r_len);
+    if (e.k > kMaxRuns) return LEY_ENOMEM;  // budget too small for the merge fan-in
+    e.in_bytes = align_up(e.r_len * rec, 256);
+    e.ws_len = ws_bytes(e.r_len);
+    e.total = kExtBufs * (e.in_bytes + e.ws_len) + kStaging * e.stg_bytes + 8 * 1024;
+    *p = e;
+    return LEY_OK;
+}
+
+static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t st) {
+    DevState* ds = dev_state();
+    if (!ds) return LEY_ECUDA;
+    ExtPlan plan;
+    const ley_status ps = external_plan(a.n, a.rec, a.kb, budget, a.tune, &plan);
+    if (ps != LEY_OK) return ps;
+    const ull q = plan.q, r_len = plan.r_len;
+    const uint32_t k = plan.k;
+    const bool long_key = a.kb > kWindow;
+    const Layout L = make_layout(r_len, true, a.tune.big);
+    const size_t stg_bytes = plan.stg_bytes, in_bytes = plan.in_bytes, ws_len = plan.ws_len;
+    const size_t total = plan.total;
     const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
     if (dbg)
         std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
@@ -1019,7 +1068,7 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     {
         HostPipe hp(st);
         if (!hp.ok) s = LEY_ECUDA;
-        const KeySpec ks = record_keyspec(a.kb);
+        const KeySpec ks = record_keyspec(a.kb, a.tune);
         cudaEvent_t stg_free[kStaging] = {};
         // buffer b and workspace b are free again once the gathers that read
         // them (kExtBufs runs or partitions back) are done
@@ -1142,7 +1191,7 @@ static ley_status run_host_keys_only(const SortArgs& a, ull budget, cudaStream_t
         cudaGetLastError();
         return LEY_ENOMEM;
     }
-    const Layout L = make_layout(a.n, true);
+    const Layout L = make_layout(a.n, true, a.tune.big);
     // chunks of n/8 records (whole tiles), between 64 Ki and 4 Mi records
     ull chunk = (ull)ceil_div_u64(a.n / 8 + 1, kPassTile) * kPassTile;
     chunk = std::max<ull>(chunk, 16ull * kPassTile);
@@ -1165,7 +1214,7 @@ static ley_status run_host_keys_only(const SortArgs& a, ull budget, cudaStream_t
         HostPipe hp(st);
         if (!hp.ok) s = LEY_ECUDA;
         Work w = make_work(ws, L, a.n, ds->err);
-        const KeySpec ks = record_keyspec(a.kb);
+        const KeySpec ks = record_keyspec(a.kb, a.tune);
         if (s == LEY_OK) s = stage_prepare(w, L, st, a.n, 0);
         hp.mark(hp.h2d, "in begin");
         cudaEvent_t ring_free[2] = {nullptr, nullptr};
@@ -1256,8 +1305,8 @@ namespace ley {
 // at submission).
 ley_status check_records_request(const ley_records_request& q, uint32_t rec_bytes,
                                  uint32_t key_bytes) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || q.n >= (1ull << 32))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096 || q.n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     if (q.n == 0) return LEY_OK;
     if (!q.in || !q.out) return LEY_EINVAL;
@@ -1296,9 +1345,9 @@ extern "C" {
 
 static ley_status sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
                                uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream,
-                               bool block) {
-    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
+                               bool block, const Tuning& tune) {
+    if (key_bytes < 1 || key_bytes > rec_bytes ||
+        rec_bytes > 4096 || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     if (n == 0) return LEY_OK;
     if (!in || !out) return LEY_EINVAL;
@@ -1313,6 +1362,7 @@ static ley_status sort_records(const void* in, void* out, uint64_t n, uint32_t r
     a.n = n;
     a.rec = rec_bytes;
     a.kb = key_bytes;
+    a.tune = tune;
     if (ki == MK_DEVICE && ko == MK_DEVICE) {
         if (!aligned16(in) || !aligned16(out)) return LEY_EINVAL;
         return run_device_sort(a, mem_budget, st);
@@ -1323,12 +1373,13 @@ static ley_status sort_records(const void* in, void* out, uint64_t n, uint32_t r
 
 ley_status ley_sort_records(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
                             uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
-    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, true);
+    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, true, cur_tuning());
 }
 
 ley_status ley_sort_records_async(const void* in, void* out, uint64_t n, uint32_t rec_bytes,
                                   uint32_t key_bytes, uint64_t mem_budget, ley_stream_t stream) {
-    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, false);
+    return sort_records(in, out, n, rec_bytes, key_bytes, mem_budget, stream, false,
+                        cur_tuning());
 }
 
 ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
@@ -1353,6 +1404,7 @@ ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
     a.idx_out = idx_out;
     a.n = n;
     a.kb = 8;
+    a.tune = cur_tuning();
     return run_device_sort(a, mem_budget, static_cast<cudaStream_t>(stream));
 }
 
@@ -1360,8 +1412,8 @@ ley_status ley_sort_keys_index(const uint64_t* keys_in, const uint32_t* idx_in,
 ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t count,
                                   uint32_t rec_bytes, uint32_t key_bytes, uint64_t mem_budget,
                                   ley_stream_t stream) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096)
         return LEY_EUNSUPPORTED;
     if (count == 0) return LEY_OK;
     if (!reqs) return LEY_EINVAL;
@@ -1384,7 +1436,7 @@ ley_status ley_sort_records_batch(const ley_records_request* reqs, uint32_t coun
     if (v.empty()) return LEY_OK;
     if (npos >= (1ull << 32)) return LEY_EUNSUPPORTED;
     return run_batch(v, npos, rec_bytes, key_bytes, false, mem_budget,
-                     static_cast<cudaStream_t>(stream));
+                     static_cast<cudaStream_t>(stream), cur_tuning());
 }
 
 ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t count,
@@ -1412,14 +1464,15 @@ ley_status ley_sort_keys_index_batch(const ley_pairs_request* reqs, uint32_t cou
     }
     if (v.empty()) return LEY_OK;
     if (npos >= (1ull << 32)) return LEY_EUNSUPPORTED;
-    return run_batch(v, npos, 8, 8, true, mem_budget, static_cast<cudaStream_t>(stream));
+    return run_batch(v, npos, 8, 8, true, mem_budget, static_cast<cudaStream_t>(stream),
+                     cur_tuning());
 }
 
 ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
                                  uint32_t key_bytes, uint32_t digit, uint32_t* order_out,
                                  uint64_t* hist_out, ley_stream_t stream) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096 || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     if (digit >= key_bytes) return LEY_EINVAL;
     if (!in || !order_out || !hist_out) return LEY_EINVAL;
@@ -1443,6 +1496,7 @@ ley_status ley_partition_records(const void* in, uint64_t n, uint32_t rec_bytes,
     a.rec = rec_bytes;
     a.kb = key_bytes;
     a.digit = digit;
+    a.tune = cur_tuning();
     return run_device_sort(a, 0, st);
 }
 
@@ -1469,8 +1523,8 @@ ley_status ley_plan_partitions(const void* const* runs, const uint64_t* run_len,
 
 ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32_t k, void* out,
                              uint32_t rec_bytes, uint32_t key_bytes, ley_stream_t stream) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096)
         return LEY_EUNSUPPORTED;
     if (k < 1 || k > 128) return LEY_EUNSUPPORTED;
     if (!run_start) return LEY_EINVAL;
@@ -1488,7 +1542,8 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const Layout L = make_layout(n, true);
+    const Tuning tune = cur_tuning();
+    const Layout L = make_layout(n, true, tune.big);
     const size_t total = L.total + align_up(sizeof(ull) * (k + 1), 256);
     void* base = nullptr;
     if (!scratch_alloc(ds, &base, total, st)) return LEY_ENOMEM;
@@ -1499,6 +1554,7 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
     a.n = n;
     a.rec = rec_bytes;
     a.kb = key_bytes;
+    a.tune = tune;
     Work w = make_work(static_cast<char*>(base), L, n, ds->err);
     ull* off_dev = reinterpret_cast<ull*>(static_cast<char*>(base) + L.total);
     ley_status s = stage_merge(a, a.in, off.data(), off_dev, k, w, L, st, ds->sms);
@@ -1508,16 +1564,29 @@ ley_status ley_merge_records(const void* runs, const uint64_t* run_start, uint32
 }
 
 ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
-                               uint64_t* bytes) {
+                               uint64_t mem_budget, uint64_t* bytes) {
     if (!bytes) return LEY_EINVAL;
-    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n >= (1ull << 32))
+    *bytes = 0;
+    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes > 4096 || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
-    if (key_bytes > kWindow) {
-        *bytes = n ? make_layout(n, true).total + long_key_extra(n) : 0;
+    if (n == 0) return LEY_OK;
+    const Tuning tune = cur_tuning();
+    if (mem_budget == 0) {  // the internal sort of device buffers
+        *bytes = key_bytes > kWindow ? make_layout(n, true, tune.big).total + long_key_extra(n)
+                                     : make_layout(n, !fused_gather(rec_bytes), tune.big).total;
         return LEY_OK;
     }
-    *bytes = n ? make_layout(n, !fused_gather(rec_bytes)).total : 0;
+    // pinned host buffers under the budget: the partial mode if it fits, else
+    // the external mode
+    const size_t part = partial_need(n, rec_bytes, key_bytes, mem_budget, tune);
+    if (part <= mem_budget) {
+        *bytes = part;
+        return LEY_OK;
+    }
+    ExtPlan plan;
+    const ley_status s = external_plan(n, rec_bytes, key_bytes, mem_budget, tune, &plan);
+    if (s != LEY_OK) return s;
+    *bytes = plan.total;
     return LEY_OK;
 }
 
@@ -1555,11 +1624,13 @@ namespace ley {
 // Times sorts of the n records at `in` (device) into `out` under a grid of
 // tunings -- Algorithm 1's two thresholds and the finishing CTAs per SM; the
 // first candidate is the default -- keeps the fastest (best of two timed
-// sorts after one warm-up) as the current tuning and returns it.
+// sorts after one warm-up) as the current tuning and returns it.  Each timed
+// sort gets its candidate as its own tuning; the current tuning is written
+// only once, at the end, so sorts that other threads start meanwhile run with
+// the tuning that was current before.
 static ley_status autotune_on(const void* in, void* out, ull n, uint32_t rec_bytes,
                               uint32_t key_bytes, cudaStream_t st, ley_tuning* best) {
     ley_status s = LEY_OK;
-    const Tuning saved = cur_tuning();
     std::vector<Tuning> cands;
     for (uint32_t big : {2048u, 1536u, 1024u})
         for (uint32_t tiny : {32u, 64u, 128u})
@@ -1575,16 +1646,10 @@ static ley_status autotune_on(const void* in, void* out, ull n, uint32_t rec_byt
     float best_ms = 1e30f;
     Tuning best_t = cands[0];
     for (size_t i = 0; i < cands.size() && s == LEY_OK; i++) {
-        {
-            std::lock_guard<std::mutex> lk(g_mu);
-            int d = 0;
-            cudaGetDevice(&d);
-            g_tune[d] = cands[i];
-        }
         float ms = 1e30f;
         for (int rep = 0; rep < 3 && s == LEY_OK; rep++) {  // first run warms up
             cudaEventRecord(e0, st);
-            s = ley_sort_records(in, out, n, rec_bytes, key_bytes, 0, st);
+            s = sort_records(in, out, n, rec_bytes, key_bytes, 0, st, true, cands[i]);
             cudaEventRecord(e1, st);
             if (s == LEY_OK && cudaEventSynchronize(e1) != cudaSuccess) s = LEY_ECUDA;
             float t = 0.f;
@@ -1597,11 +1662,11 @@ static ley_status autotune_on(const void* in, void* out, ull n, uint32_t rec_byt
         }
     }
     if (s == LEY_OK) s = ley_last_device_status(st);
-    {
+    if (s == LEY_OK) {
         std::lock_guard<std::mutex> lk(g_mu);
         int d = 0;
         cudaGetDevice(&d);
-        g_tune[d] = s == LEY_OK ? best_t : saved;
+        g_tune[d] = best_t;
     }
     if (best) {
         best->big_bucket = best_t.big;
@@ -1619,8 +1684,8 @@ extern "C" {
 
 ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
                                 uint64_t seed, ley_tuning* best) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096 || n == 0 || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     DevState* ds = dev_state();
     if (!ds) return LEY_ECUDA;
@@ -1643,9 +1708,9 @@ ley_status ley_autotune_records(uint64_t n, uint32_t rec_bytes, uint32_t key_byt
 }
 
 ley_status ley_autotune_records_on(const void* in, uint64_t n, uint32_t rec_bytes,
-                                   uint32_t key_bytes, ley_tuning* best) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u) || n == 0 || n >= (1ull << 32))
+                                   uint32_t key_bytes, ley_tuning* best, ley_stream_t stream) {
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096 || n == 0 || n >= (1ull << 32))
         return LEY_EUNSUPPORTED;
     if (!in) return LEY_EINVAL;
     if (mem_kind(in) != MK_DEVICE || !aligned16(in)) return LEY_EINVAL;
@@ -1653,6 +1718,20 @@ ley_status ley_autotune_records_on(const void* in, uint64_t n, uint32_t rec_byte
     if (!ds) return LEY_ECUDA;
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEY_ECUDA;
+    // The timed sorts read `in` only after the work the caller queued on
+    // `stream` before this call (which may still be writing it).
+    {
+        cudaEvent_t ready = nullptr;
+        const bool ok = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventRecord(ready, static_cast<cudaStream_t>(stream)) == cudaSuccess &&
+                        cudaStreamWaitEvent(st, ready, 0) == cudaSuccess;
+        if (ready) cudaEventDestroy(ready);
+        if (!ok) {
+            cudaGetLastError();
+            cudaStreamDestroy(st);
+            return LEY_ECUDA;
+        }
+    }
     void* out = nullptr;
     ley_status s = LEY_OK;
     if (!scratch_alloc(ds, &out, align_up(n * rec_bytes, 256), st)) s = LEY_ENOMEM;
@@ -1851,7 +1930,7 @@ static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const L
     }
     LaunchCfg cf{sms * blocks_per_sm(KK_FINISH_REC), kFinThreads, kernel_smem(KK_FINISH_REC), st};
     LEY_TRY(launch_finish_records(cf, w, ks));
-    const int gv = a.rec == 100 ? (gather_variant() == 0 ? 0 : 1) : 0;
+    const int gv = a.rec == 100 ? 1 : 0;
     const KernelKind gk = a.rec != 100 ? KK_GATHER_GENERIC
                                        : (gv == 1 ? KK_GATHER100_TMA : KK_GATHER100);
     LaunchCfg cg{sms * blocks_per_sm(gk), 0, 0, st};
@@ -1864,8 +1943,8 @@ static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const L
 extern "C" ley_status ley_sort_records_noalloc(const void* in, void* out, uint64_t n,
                                                uint32_t rec_bytes, uint32_t key_bytes,
                                                ley_stream_t stream) {
-    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes || rec_bytes < 4 ||
-        rec_bytes > 4096 || (rec_bytes & 3u))
+    if (key_bytes < 1 || key_bytes > 12 || key_bytes > rec_bytes ||
+        rec_bytes > 4096)
         return LEY_EUNSUPPORTED;
     if (n > kNoAllocMaxRecords) return LEY_ENOMEM;
     if (n == 0) return LEY_OK;

@@ -192,19 +192,42 @@ k_gather100_tma(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
 
 // ------------------------------------------------------------ generic path
 
-// Any rec_bytes that is a multiple of 4: one warp copies one record.
+// Any rec_bytes.  A multiple of 4 is copied in words, one warp per record.
+// Other sizes are copied byte by byte, one warp per 32 consecutive output
+// records: lane l loads the source index of record l of the group, and the
+// warp writes the group's cnt * rec output bytes contiguously, each lane
+// taking the source index of its byte's record from the lane that loaded it.
 __global__ void __launch_bounds__(256)
 k_gather_generic(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                  const uint32_t* __restrict__ perm, ull n, ull n_in, uint32_t rec) {
     const int lane = threadIdx.x & 31;
     const ull warps = (ull)gridDim.x * (blockDim.x >> 5);
-    const uint32_t words = rec / 4;
-    for (ull j = (ull)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
-        uint32_t pj = __ldg(perm + j);
+    const ull warp0 = (ull)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if ((rec & 3u) == 0) {
+        const uint32_t words = rec / 4;
+        for (ull j = warp0; j < n; j += warps) {
+            uint32_t pj = __ldg(perm + j);
+            if (pj >= n_in) pj = 0;  // never for a valid permutation; keeps reads in bounds
+            const uint32_t* s = reinterpret_cast<const uint32_t*>(in + (ull)pj * rec);
+            uint32_t* d = reinterpret_cast<uint32_t*>(out + j * rec);
+            for (uint32_t q = lane; q < words; q += 32) d[q] = __ldg(s + q);
+        }
+        return;
+    }
+    const ull groups = (n + 31) / 32;
+    for (ull g = warp0; g < groups; g += warps) {
+        const ull j0 = g * 32;
+        const uint32_t cnt = (uint32_t)min((ull)32, n - j0);
+        uint32_t pj = (uint32_t)lane < cnt ? __ldg(perm + j0 + lane) : 0u;
         if (pj >= n_in) pj = 0;  // never for a valid permutation; keeps reads in bounds
-        const uint32_t* s = reinterpret_cast<const uint32_t*>(in + (ull)pj * rec);
-        uint32_t* d = reinterpret_cast<uint32_t*>(out + j * rec);
-        for (uint32_t q = lane; q < words; q += 32) d[q] = __ldg(s + q);
+        const uint32_t bytes = cnt * rec;
+        uint8_t* d = out + j0 * rec;
+        for (uint32_t b0 = 0; b0 < bytes; b0 += 32) {  // the same trip count on every lane
+            const uint32_t b = b0 + (uint32_t)lane;
+            const uint32_t r = min(b / rec, cnt - 1);
+            const uint32_t p = __shfl_sync(0xffffffffu, pj, (int)r);
+            if (b < bytes) d[b] = __ldg(in + (ull)p * rec + (b - r * rec));
+        }
     }
 }
 

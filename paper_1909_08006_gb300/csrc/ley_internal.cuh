@@ -138,24 +138,6 @@ struct Work {
     unsigned long long n;
 };
 
-// Optional per-phase cycle counters for tracing kernel internals; compiled
-// in only with -DLEY_PHASE_TIMING (never in the library build).  Thread 0 of
-// each CTA adds the cycles since its previous mark to counter k.
-#ifdef LEY_PHASE_TIMING
-#define LEY_PHASE_BEGIN long long ley_tp_ = clock64()
-#define LEY_PHASE(k)                                                             \
-    do {                                                                         \
-        if (threadIdx.x == 0) {                                                  \
-            long long t_ = clock64();                                            \
-            atomicAdd(&g_ley_phase[k], (unsigned long long)(t_ - ley_tp_));      \
-            ley_tp_ = t_;                                                        \
-        }                                                                        \
-    } while (0)
-#else
-#define LEY_PHASE_BEGIN
-#define LEY_PHASE(k)
-#endif
-
 // One request of a batched sort.  Requests lie back to back in the batch's
 // tuple space, each starting on a tile boundary: request r owns tuple
 // positions [off, off + n), and its tuples carry indices local to it.

@@ -29,10 +29,6 @@ namespace ley {
 
 using ull = unsigned long long;
 
-#ifdef LEY_PHASE_TIMING
-__device__ unsigned long long g_ley_phase[64];
-#endif
-
 // ------------------------------------------------------------- helpers
 
 // Programmatic dependent launch: the level kernels are launched so that the
@@ -522,7 +518,8 @@ k_batch_extract_pairs(const BatchReq* __restrict__ reqs, const uint32_t* __restr
     }
 }
 
-// Records of any size: out_r[j] = in_r[perm[off_r + j]], one warp per record.
+// Records of any size: out_r[j] = in_r[perm[off_r + j]], one warp per record
+// (in words when the size is a multiple of 4, else in bytes).
 __global__ void __launch_bounds__(256)
 k_batch_gather_generic(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ tile_req,
                        const uint32_t* __restrict__ perm, ull npos, uint32_t rec, uint32_t* err) {
@@ -538,9 +535,15 @@ k_batch_gather_generic(const BatchReq* __restrict__ reqs, const uint32_t* __rest
             if (lane == 0) LEY_FAIL(err, kErrCapacity);
             pj = 0;
         }
-        const uint32_t* sp = reinterpret_cast<const uint32_t*>(q.in + (ull)pj * rec);
-        uint32_t* dp = reinterpret_cast<uint32_t*>(q.out + (pos - q.off) * rec);
-        for (uint32_t k = lane; k < words; k += 32) dp[k] = __ldg(sp + k);
+        if ((rec & 3u) == 0) {
+            const uint32_t* sp = reinterpret_cast<const uint32_t*>(q.in + (ull)pj * rec);
+            uint32_t* dp = reinterpret_cast<uint32_t*>(q.out + (pos - q.off) * rec);
+            for (uint32_t k = lane; k < words; k += 32) dp[k] = __ldg(sp + k);
+        } else {  // record sizes that are not a multiple of 4: bytes
+            const uint8_t* sp = q.in + (ull)pj * rec;
+            uint8_t* dp = q.out + (pos - q.off) * rec;
+            for (uint32_t k = lane; k < rec; k += 32) dp[k] = __ldg(sp + k);
+        }
     }
 }
 
@@ -1051,7 +1054,6 @@ k_pass(Work w, KeySpec ks, int L) {
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
-    LEY_PHASE_BEGIN;
     // Thread 0 asks the L2 for the CTA's tiles one tile ahead: while tile t
     // is scattered, tile t + grid is being fetched and tile t + 2 grid is
     // looked up in steps (owner, then bucket), so no lookup is waited for.
@@ -1074,7 +1076,6 @@ k_pass(Work w, KeySpec ks, int L) {
             continue;
         }
         __syncthreads();  // previous tile's shared state is no longer read
-        LEY_PHASE(0);
         for (int i = tid; i < kPassWarps * kRadix; i += kPassThreads) (&wcnt[0][0])[i] = 0;
         const uint32_t lt = t - tile0;
         const ull base = sg.start + (ull)lt * kPassTile;
@@ -1098,13 +1099,6 @@ k_pass(Work w, KeySpec ks, int L) {
             v[k] = idx < m ? src[base + idx] : make_uint4(0, 0, 0, 0);
         }
         __syncthreads();  // counters zeroed
-#ifdef LEY_PHASE_TIMING
-        if (tid == 0) {  // thread 0 waits for its own loads
-            volatile uint32_t sink = v[0].x ^ v[kPassItems - 1].w;
-            (void)sink;
-        }
-#endif
-        LEY_PHASE(6);
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
             const uint32_t idx = warp * (kPassItems * 32) + k * 32 + lane;
@@ -1112,9 +1106,7 @@ k_pass(Work w, KeySpec ks, int L) {
             const uint32_t dk = valid ? digit_of(v[k], d) : 0u;
             rd[k] = (warp_rank(wcnt[warp], dk, valid, lt_mask, lane) << 8) | dk;
         }
-        LEY_PHASE(5);
         __syncthreads();
-        LEY_PHASE(1);
         Seg sgn;
         uint32_t tbn = 0;
         if (tid == 0 && sn < nseg) {
@@ -1149,7 +1141,6 @@ k_pass(Work w, KeySpec ks, int L) {
             gbase[tid] = gb;
         }
         __syncthreads();
-        LEY_PHASE(2);
         // Stage the tile in shared memory in sorted-by-digit order.
 #pragma unroll
         for (int k = 0; k < kPassItems; k++) {
@@ -1162,7 +1153,6 @@ k_pass(Work w, KeySpec ks, int L) {
             }
         }
         __syncthreads();
-        LEY_PHASE(3);
         if (tid == 0 && sn < nseg && tn >= tbn && sgn.buf <= 1 && sgn.start + sgn.count <= w.n) {
             const ull off = (ull)(tn - tbn) * kPassTile;
             if (off < sgn.count) {
@@ -1179,7 +1169,6 @@ k_pass(Work w, KeySpec ks, int L) {
             if (pos >= sg.start && pos < seg_end) dst[pos] = tv;
             else LEY_FAIL(w.err, kErrCapacity);
         }
-        LEY_PHASE(4);
     }
 }
 
@@ -1352,14 +1341,10 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             v[k] = idx < c ? B[r0 + idx] : ref;
     }
     int ds = d0 < ks.ndig ? d0 : ks.ndig - 1;
-    for (int attempt = 0;; attempt++) {
+    for (;;) {
 #pragma unroll
         for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
         __syncthreads();  // counters zeroed (and, first time, all reads of B done)
-#ifdef LEY_PHASE_TIMING
-        if (FROM_GLOBAL && attempt == 0 && threadIdx.x == 0)
-            atomicAdd(&g_ley_phase[20], (unsigned long long)clock64());
-#endif
 #pragma unroll
         for (int k = 0; k < kFinItems; k++) {
             const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
@@ -1441,9 +1426,6 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
         if (sc > (uint32_t)kWarpMax) stack_push(S, s2, sc, ds + 1, err);
         else if (sc > ks.tiny) queue_push(S, s2, sc, ds + 1, err);
     }
-#ifdef LEY_PHASE_TIMING
-    if (FROM_GLOBAL && threadIdx.x == 0) atomicAdd(&g_ley_phase[21], (unsigned long long)clock64());
-#endif
     // Tiny sub-buckets: rank by comparison (ComparisonSort of Algorithm 1).
     for (uint32_t i = tid; i < c; i += kFinThreads) {
         const uint4 tv = B[r0 + i];
@@ -1719,10 +1701,8 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     constexpr int TM = TaskEmit<MODE>::mode;  // how a task is emitted
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
     if (tid == 0) S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
-    LEY_PHASE_BEGIN;
     while (true) {
         __syncthreads();
-        LEY_PHASE(10);
         const uint32_t ti = S.task;
         if (ti >= nfin) break;
         const FinTask tk = w.fin[ti];
@@ -1733,7 +1713,6 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             next = atomicAdd(&w.ctl->fin_ctr, 1u);
             S.q_head = S.q_tail = S.q_pending = S.bs_n = 0;
         }
-        LEY_PHASE(11);
         bool skip = false;
         if (tk.start + tk.count > w.n || tk.buf > 1 ||
             (!(tk.flags & 1) && tk.count > (uint32_t)kSmall)) {  // never for a valid task list
@@ -1754,7 +1733,6 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
         if (!skip) {
             fin_block_pass<true>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
             __syncthreads();
-            LEY_PHASE(12);
             while (S.q_tail != 0 || S.bs_n != 0) {
                 fin_drain_queue(B, S, ks, w.err);
                 __syncthreads();
@@ -1776,7 +1754,6 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                 fin_block_pass<false>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
                 __syncthreads();
             }
-            LEY_PHASE(13);
             if constexpr (TM == 2) {
                 // The task's source indices in final order (count <= kSmall
                 // entries over the counters, which are free now), then the
@@ -1803,7 +1780,6 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                     te(tk.start + j, B[o]);
                 }
             }
-            LEY_PHASE(14);
         }
         __syncthreads();
         if (tid == 0) S.task = next;
@@ -1820,17 +1796,6 @@ __global__ void k_partition_out(Work w, ull n, uint32_t* order_out, ull* hist_ou
 }
 
 // -------------------------------------------------------------- launchers
-#ifdef LEY_PHASE_TIMING
-}  // namespace ley
-extern "C" int ley_phase_read(unsigned long long* out) {
-    cudaMemcpyFromSymbol(out, ley::g_ley_phase, sizeof(unsigned long long) * 64);
-    static unsigned long long zero[64];
-    cudaMemcpyToSymbol(ley::g_ley_phase, zero, sizeof(zero));
-    return 0;
-}
-namespace ley {
-#endif
-
 cudaError_t launch_extract_window(const LaunchCfg& c, const uint8_t* in, const uint32_t* order,
                                   ull n, uint32_t rec, uint32_t koff, KeySpec ks, const Work& w) {
     const int grid = (int)min((uint32_t)c.grid, ceil_div_u64(n, kPassTile));

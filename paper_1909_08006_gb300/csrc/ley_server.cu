@@ -43,12 +43,15 @@ struct SrvReq {
     uint32_t rec_bytes, key_bytes;
     ull bytes;  // device bytes charged while the request is in flight
     double t_submit, t_start, t_done;
+    double dev_start, dev_done;  // device clock: the batch's start and completion events
+    ull batch;                   // number of the batch that carried it
     int status;  // -1 pending, else ley_status
 };
 
 struct Batch {
     int slot;
-    cudaEvent_t done;
+    ull id;
+    cudaEvent_t start, done;  // timing events on the slot stream around the batch's work
     std::vector<ull> tickets;
     ull bytes;
     double t_launch;
@@ -72,6 +75,9 @@ struct ley_server {
     bool stop = false, sched_done = false;
     std::thread sched, compl_;
     ley::Clock::time_point t0 = ley::Clock::now();
+    // Recorded when the server is created: the origin of the device-clock
+    // batch intervals (cudaEventElapsedTime against it).
+    cudaEvent_t t0_ev = nullptr;
 
     double now() const {
         return std::chrono::duration<double>(ley::Clock::now() - t0).count();
@@ -151,8 +157,16 @@ static void scheduler(ley_server* S) {
             it->second.push_back(r.rec);
         }
         cudaStream_t st = S->slots[slot];
+        const ull batch_id = S->launched_batches + 1;
         lk.unlock();
         ley_status s = LEY_OK;
+        // The batch's device interval: from a timing event recorded on its
+        // slot stream before its first launch to its completion event.
+        cudaEvent_t ev0 = nullptr;
+        if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventRecord(ev0, st) != cudaSuccess) {
+            cudaGetLastError();
+            s = LEY_ECUDA;
+        }
         for (auto& g : geo)
             if (s == LEY_OK)
                 s = ley_sort_records_batch(g.second.data(), (uint32_t)g.second.size(), g.first.first,
@@ -160,8 +174,7 @@ static void scheduler(ley_server* S) {
         if (s == LEY_OK && !pq.empty())
             s = ley_sort_keys_index_batch(pq.data(), (uint32_t)pq.size(), 0, st);
         cudaEvent_t ev = nullptr;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventRecord(ev, st) != cudaSuccess) {
+        if (cudaEventCreate(&ev) != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess) {
             cudaGetLastError();
             if (s == LEY_OK) s = LEY_ECUDA;
         }
@@ -169,6 +182,7 @@ static void scheduler(ley_server* S) {
         if (s != LEY_OK) {  // nothing (more) in flight for this batch
             if (ev) cudaEventSynchronize(ev);
             if (ev) cudaEventDestroy(ev);
+            if (ev0) cudaEventDestroy(ev0);
             const double t = S->now();
             for (ull tk : take) {
                 SrvReq& r = S->reqs[tk];
@@ -181,7 +195,7 @@ static void scheduler(ley_server* S) {
             continue;
         }
         S->launched_batches++;
-        S->inflight.push_back(Batch{slot, ev, std::move(take), bytes, t_launch});
+        S->inflight.push_back(Batch{slot, batch_id, ev0, ev, std::move(take), bytes, t_launch});
         S->cv_done.notify_all();
     }
     S->sched_done = true;
@@ -199,6 +213,13 @@ static void completer(ley_server* S) {
         const cudaError_t e = cudaEventSynchronize(b.done);
         const double t = S->now();
         ley_status st = e == cudaSuccess ? ley_last_device_status(S->slots[b.slot]) : LEY_ECUDA;
+        float ms0 = 0.f, ms1 = 0.f;
+        if (e == cudaSuccess && (cudaEventElapsedTime(&ms0, S->t0_ev, b.start) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms1, S->t0_ev, b.done) != cudaSuccess)) {
+            cudaGetLastError();
+            ms0 = ms1 = -1.f;  // not timed (reported as negative)
+        }
+        cudaEventDestroy(b.start);
         cudaEventDestroy(b.done);
         lk.lock();
         S->inflight.pop_front();
@@ -206,6 +227,9 @@ static void completer(ley_server* S) {
             SrvReq& r = S->reqs[tk];
             r.status = st;
             r.t_done = t;
+            r.dev_start = ms0 * 1e-3;
+            r.dev_done = ms1 * 1e-3;
+            r.batch = b.id;
         }
         S->in_use -= b.bytes;
         S->slot_busy[b.slot] = false;
@@ -221,6 +245,8 @@ static ley_status submit(ley_server* S, SrvReq r, uint64_t* ticket) {
     r.bytes = request_bytes(r);
     r.t_submit = S->now();
     r.t_start = r.t_done = 0;
+    r.dev_start = r.dev_done = -1;
+    r.batch = 0;
     r.status = -1;
     S->reqs[r.ticket] = r;
     S->pending.push_back(r.ticket);
@@ -255,6 +281,14 @@ ley_status ley_server_create(ley_server** out, uint64_t mem_budget, uint32_t max
             delete S;
             return LEY_ECUDA;
         }
+    }
+    if (cudaEventCreate(&S->t0_ev) != cudaSuccess || cudaEventRecord(S->t0_ev, S->slots[0]) != cudaSuccess ||
+        cudaEventSynchronize(S->t0_ev) != cudaSuccess) {
+        cudaGetLastError();
+        if (S->t0_ev) cudaEventDestroy(S->t0_ev);
+        for (auto& t : S->slots) cudaStreamDestroy(t);
+        delete S;
+        return LEY_ECUDA;
     }
     S->sched = std::thread(scheduler, S);
     S->compl_ = std::thread(completer, S);
@@ -306,6 +340,9 @@ ley_status ley_server_wait(ley_server* S, uint64_t ticket, ley_server_times* tim
         times->submit_s = r.t_submit;
         times->start_s = r.t_start;
         times->done_s = r.t_done;
+        times->dev_start_s = r.dev_start;
+        times->dev_done_s = r.dev_done;
+        times->batch = r.batch;
     }
     const ley_status st = (ley_status)r.status;
     S->reqs.erase(ticket);
@@ -333,6 +370,7 @@ ley_status ley_server_destroy(ley_server* S) {
     S->sched.join();
     S->compl_.join();
     for (auto& s : S->slots) cudaStreamDestroy(s);
+    if (S->t0_ev) cudaEventDestroy(S->t0_ev);
     delete S;
     return LEY_OK;
 }

@@ -72,8 +72,36 @@ def test_host_only_entry_points(ley):
     assert e.value.status == ley.LEY_EUNSUPPORTED
     # keys longer than 12 bytes: a permutation and two order arrays more
     assert ley.ley_workspace_bytes(100_000_000, key_bytes=30) > b + 12 * 100_000_000 - 1
-    with pytest.raises(ley.LeyError):
-        ley.ley_workspace_bytes(10, rec_bytes=102, key_bytes=10)
+    # any record size from key_bytes to 4096 bytes (not only multiples of 4)
+    assert ley.ley_workspace_bytes(100_000_000, rec_bytes=102) == b104
+    assert ley.ley_workspace_bytes(1000, rec_bytes=10, key_bytes=10) > 0
+    assert ley.ley_workspace_bytes(1000, rec_bytes=1, key_bytes=1) > 0
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_workspace_bytes(10, rec_bytes=4097, key_bytes=10)
+    assert e.value.status == ley.LEY_EUNSUPPORTED
+
+
+def test_workspace_bytes_under_a_budget(ley):
+    # host-memory sorts under a device budget (Section 4.1's 20 GB partially
+    # in-memory and 60 GB external data sets under a 30 GB limit)
+    budget = 30_000_000_000
+    n = 200_000_000
+    part = ley.ley_workspace_bytes(n, mem_budget=budget)
+    internal = ley.ley_workspace_bytes(n, rec_bytes=104)  # with the permutation
+    # the partial mode holds the input, one workspace and four staging buffers
+    assert n * 100 + internal <= part <= n * 100 + internal + 4 * (64 << 20) + 4096
+    assert part <= budget
+    n = 600_000_000
+    ext = ley.ley_workspace_bytes(n, mem_budget=budget)
+    assert 0 < ext <= budget  # the external mode's rotating buffers fit the cap
+    assert ext < n * 100
+    # a budget that holds no mode at all
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_workspace_bytes(n, mem_budget=1 << 20)
+    assert e.value.status == ley.LEY_ENOMEM
+    # the budget never changes the answer for the internal sort of device
+    # buffers (mem_budget 0), and n == 0 needs nothing
+    assert ley.ley_workspace_bytes(0, mem_budget=budget) == 0
 
 
 def test_argument_checks_before_any_gpu_work(ley):

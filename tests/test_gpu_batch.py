@@ -62,7 +62,7 @@ def test_records_batch_matches_each_request_alone(orc, ley, kinds):
         assert (b[:256] == 0xA5).all() and (b[256 + n * 100:] == 0xA5).all()
 
 
-@pytest.mark.parametrize("rec_bytes,key_bytes", [(104, 10), (16, 12), (8, 3)])
+@pytest.mark.parametrize("rec_bytes,key_bytes", [(104, 10), (16, 12), (8, 3), (10, 10), (13, 5)])
 def test_records_batch_other_geometries(orc, ley, rec_bytes, key_bytes):
     reqs, want = [], []
     for i, n in enumerate([1, 4097, 3, 20_000, 4096]):

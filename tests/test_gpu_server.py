@@ -1,9 +1,11 @@
 """GPU tests of the continuous-batching sort server.
 
-Every request's result must be byte-identical to the same request sorted
-alone with the single-request call, whatever it was batched with; admission
-keeps the memory charged to admitted requests within the budget; requests
-submitted from several threads while batches run all complete.
+Every request's result must be byte-identical to the CPU oracle's sort of
+the same request (the stable order of Section 3.1's reading) and to the same
+request sorted alone with the single-request call, whatever it was batched
+with; admission keeps the memory charged to admitted requests within the
+budget; requests submitted from several threads while batches run all
+complete, and batches on different launch slots overlap on the device clock.
 """
 import threading
 import time
@@ -29,26 +31,32 @@ def ley():
     return m
 
 
-def _make_requests(ley, count, seed, max_n=60_000):
+def _make_requests(ley, orc, count, seed, max_n=60_000):
+    """Requests with three answers each: the server's output buffer, the
+    single-request call's output, and the oracle's sort (host arrays)."""
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(count):
         n = int(np.exp(rng.uniform(0, np.log(max_n))))
         if i % 2 == 0:
             gen = datagen.skew_records if i % 4 == 0 else datagen.uniform_records
-            x = gen(n, seed=seed * 1000 + i).to(DEV)
+            h = gen(n, seed=seed * 1000 + i)
+            x = h.to(DEV)
             alone = torch.empty_like(x)
             ley.ley_sort_records(x, alone)
-            reqs.append(("rec", x, torch.empty_like(x), alone))
+            want = orc.sort_records(h.numpy())
+            reqs.append(("rec", x, torch.empty_like(x), alone, want))
         else:
             if i % 3 == 0:
                 k, v = datagen.narrow_pairs(n, seed=seed * 1000 + i, distinct=7)
             else:
                 k, v = datagen.uniform_pairs(n, seed=seed * 1000 + i)
+            want = orc.sort_keys_index(k.numpy(), v.numpy())
             k, v = k.to(DEV), v.to(DEV)
             ak, av = torch.empty_like(k), torch.empty_like(v)
             ley.ley_sort_keys_index(k, v, ak, av)
-            reqs.append(("pairs", (k, v), (torch.empty_like(k), torch.empty_like(v)), (ak, av)))
+            reqs.append(("pairs", (k, v), (torch.empty_like(k), torch.empty_like(v)), (ak, av),
+                         want))
     torch.cuda.synchronize()
     return reqs
 
@@ -61,13 +69,30 @@ def _submit(ley, srv, r):
 
 
 def _same(r):
+    """The served result equals the oracle's and the request sorted alone."""
     if r[0] == "rec":
-        return torch.equal(r[2], r[3])
-    return torch.equal(r[2][0], r[3][0]) and torch.equal(r[2][1], r[3][1])
+        got = r[2].cpu().numpy()
+        return np.array_equal(got, r[4]) and torch.equal(r[2], r[3])
+    gk = r[2][0].cpu().numpy().view(np.uint64)
+    gv = r[2][1].cpu().numpy().view(np.uint32)
+    return (np.array_equal(gk, r[4][0]) and np.array_equal(gv, r[4][1])
+            and torch.equal(r[2][0], r[3][0]) and torch.equal(r[2][1], r[3][1]))
 
 
-def test_results_identical_alone_and_in_the_mix(ley):
-    reqs = _make_requests(ley, 120, seed=1)
+def _overlapping_batches(times):
+    """Pairs of distinct batches whose device-clock intervals overlap (two
+    batches of one launch slot never do: the slot's stream runs them in turn)."""
+    iv = {}
+    for t in times:
+        assert t["dev_done_s"] >= t["dev_start_s"] >= 0.0
+        iv[t["batch"]] = (t["dev_start_s"], t["dev_done_s"])
+    spans = sorted(iv.items(), key=lambda kv: kv[1][0])
+    return [(a[0], b[0]) for i, a in enumerate(spans) for b in spans[i + 1:]
+            if b[1][0] < a[1][1]]
+
+
+def test_results_identical_alone_and_in_the_mix(ley, orc):
+    reqs = _make_requests(ley, orc, 120, seed=1)
     srv = ley.ley_server_create(8 << 30, max_batch=32, slots=3)
     try:
         tickets = [_submit(ley, srv, r) for r in reqs]
@@ -80,8 +105,8 @@ def test_results_identical_alone_and_in_the_mix(ley):
     assert all(t["submit_s"] <= t["start_s"] <= t["done_s"] for t in times)
 
 
-def test_arrivals_while_batches_run_from_several_threads(ley):
-    reqs = _make_requests(ley, 96, seed=2)
+def test_arrivals_while_batches_run_from_several_threads(ley, orc):
+    reqs = _make_requests(ley, orc, 96, seed=2)
     srv = ley.ley_server_create(4 << 30, max_batch=16, slots=3)
     tickets = [None] * len(reqs)
 
@@ -102,15 +127,15 @@ def test_arrivals_while_batches_run_from_several_threads(ley):
         ley.ley_server_destroy(srv)
     assert all(_same(r) for r in reqs)
     assert st["pending"] == 0 and st["inflight_batches"] == 0 and st["bytes_in_use"] == 0
-    # batches ran on several slots at once: some requests overlap in time
-    # without having started together
-    spans = sorted((t["start_s"], t["done_s"]) for t in times)
-    assert any(b[0] > a[0] and b[0] < a[1] for a, b in zip(spans, spans[1:])) or \
-        st["launched_batches"] >= 2
+    # requests admitted while others were on the GPU: at least two batches
+    # were in progress on the device at the same time (device-clock events)
+    assert st["launched_batches"] >= 2
+    assert _overlapping_batches(times), sorted(
+        {(t["batch"], t["dev_start_s"], t["dev_done_s"]) for t in times})
 
 
-def test_admission_respects_the_budget(ley):
-    reqs = _make_requests(ley, 40, seed=3, max_n=200_000)
+def test_admission_respects_the_budget(ley, orc):
+    reqs = _make_requests(ley, orc, 40, seed=3, max_n=200_000)
     budget = 96 << 20  # a few requests at a time
     srv = ley.ley_server_create(budget, max_batch=64, slots=2)
     seen = []
@@ -137,8 +162,8 @@ def test_admission_respects_the_budget(ley):
     assert st["launched_batches"] >= 3  # the budget forced several batches
 
 
-def test_request_larger_than_budget_runs_alone(ley):
-    reqs = _make_requests(ley, 6, seed=4, max_n=300_000)
+def test_request_larger_than_budget_runs_alone(ley, orc):
+    reqs = _make_requests(ley, orc, 6, seed=4, max_n=300_000)
     srv = ley.ley_server_create(64 << 10, max_batch=64, slots=2)  # smaller than any request
     try:
         tickets = [_submit(ley, srv, r) for r in reqs]
@@ -150,9 +175,10 @@ def test_request_larger_than_budget_runs_alone(ley):
     assert st["launched_batches"] == len(reqs)
     spans = sorted((t["start_s"], t["done_s"]) for t in times)
     assert all(b[0] >= a[1] for a, b in zip(spans, spans[1:]))  # one at a time
+    assert not _overlapping_batches(times)  # and one at a time on the device
 
 
-def test_server_errors(ley):
+def test_server_errors(ley, orc):
     with pytest.raises(ley.LeyError):
         ley.ley_server_create(0)
     srv = ley.ley_server_create(1 << 30)
@@ -169,11 +195,11 @@ def test_server_errors(ley):
             ley.ley_server_submit_records(srv, h, torch.empty_like(x))  # host memory
         assert e.value.status == ley.LEY_EINVAL
         # the server still serves after rejections
-        y = datagen.uniform_records(5000, seed=9).to(DEV)
-        out, alone = torch.empty_like(y), torch.empty_like(y)
-        ley.ley_sort_records(y, alone)
+        h = datagen.uniform_records(5000, seed=9)
+        y = h.to(DEV)
+        out = torch.empty_like(y)
         ley.ley_server_wait(srv, ley.ley_server_submit_records(srv, y, out))
-        assert torch.equal(out, alone)
+        assert np.array_equal(out.cpu().numpy(), orc.sort_records(h.numpy()))
         with pytest.raises(ley.LeyError):
             ley.ley_server_wait(srv, 999_999)  # unknown ticket
     finally:

@@ -105,18 +105,13 @@ def test_skew_one_million(orc, ley):
 
 
 @pytest.mark.parametrize("rec_bytes,key_bytes", [(16, 12), (8, 1), (104, 10), (100, 4),
-                                                 (12, 12), (4096, 7), (20, 9)])
+                                                 (12, 12), (4096, 7), (20, 9), (10, 10), (1, 1),
+                                                 (3, 2), (13, 7), (102, 10), (4095, 12)])
 def test_other_geometries_exact(orc, ley, rec_bytes, key_bytes):
     n = 20_000 if rec_bytes < 1000 else 2_000
     rec = datagen.uniform_records(n, seed=rec_bytes, rec_bytes=rec_bytes)
     rec[:, :key_bytes] &= 0x3  # ties on every byte
     check_exact(orc, ley, rec, key_bytes=key_bytes)
-
-
-def test_lsu_gather_variant_exact(orc, ley, monkeypatch):
-    monkeypatch.setenv("LEY_GATHER", "lsu")
-    for n in [1, 31, 33, 4096, 100_003]:
-        check_exact(orc, ley, datagen.uniform_records(n, seed=n + 5))
 
 
 def test_separate_tma_gather_variant_exact(orc, ley, monkeypatch):

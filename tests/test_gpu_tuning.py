@@ -106,3 +106,66 @@ def test_autotuner_on_callers_records_leaves_them_and_stays_exact(orc, ley):
         assert e.value.status == ley.LEY_EINVAL
     finally:
         ley.ley_set_tuning(None)
+
+
+def test_tuning_changes_while_sorts_run_never_fail_them(orc, ley):
+    # One thread keeps changing the tuning (big-bucket threshold 256..2048)
+    # and another runs the autotuner on its own records, while this thread
+    # sorts on its own stream and serves requests through a server.  Every
+    # sort reads the tuning once when it starts, so none of them may fail
+    # (a layout sized for one threshold and run with another would) and every
+    # result must match the oracle.
+    import threading
+    rec = datagen.skew_records(600_000, seed=31)
+    want = orc.sort_records(rec.numpy())
+    d_in = rec.to(DEV)
+    tune_in = datagen.uniform_records(200_000, seed=32).to(DEV)
+    small = [datagen.uniform_records(20_000 + 997 * i, seed=40 + i) for i in range(12)]
+    small_want = [orc.sort_records(x.numpy()) for x in small]
+    small_dev = [x.to(DEV) for x in small]
+    torch.cuda.synchronize()
+    stop = threading.Event()
+    errors = []
+
+    def flip():
+        k = 0
+        try:
+            while not stop.is_set():
+                ley.ley_set_tuning(TUNINGS[k % len(TUNINGS)])
+                k += 1
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(e)
+
+    def autotune():
+        try:
+            torch.cuda.set_device(0)
+            ley.ley_autotune_records_on(tune_in, key_bytes=10)
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+
+    th = [threading.Thread(target=flip), threading.Thread(target=autotune)]
+    for t in th:
+        t.start()
+    try:
+        s1 = torch.cuda.Stream()
+        d_out = torch.empty_like(d_in)
+        for _ in range(12):
+            ley.ley_sort_records(d_in, d_out, stream=s1)
+            assert ley.ley_last_device_status(s1) == ley.LEY_OK
+            assert np.array_equal(d_out.cpu().numpy(), want)
+        srv = ley.ley_server_create(2 << 30, max_batch=4, slots=2)
+        try:
+            outs = [torch.empty_like(x) for x in small_dev]
+            tickets = [ley.ley_server_submit_records(srv, x, o) for x, o in zip(small_dev, outs)]
+            for t in tickets:
+                ley.ley_server_wait(srv, t)
+        finally:
+            ley.ley_server_destroy(srv)
+        for o, w in zip(outs, small_want):
+            assert np.array_equal(o.cpu().numpy(), w)
+    finally:
+        stop.set()
+        for t in th:
+            t.join()
+        ley.ley_set_tuning(None)
+    assert not errors, errors
