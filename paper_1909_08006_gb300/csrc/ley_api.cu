@@ -925,8 +925,9 @@ static std::vector<std::vector<ull>> plan_partitions(const std::vector<HostRun>&
 }
 
 // Merge of the k sorted runs whose records lie back to back at dev_runs (run r
-// at [off[r], off[r+1]) records, off on the host): tuples, ceil(log2 k)
-// merge-path rounds, the permutation in w.perm.  Queued on st.
+// at [off[r], off[r+1]) records, off on the host): tuples, then the k-way
+// merge path in one pass (pairwise merge-path rounds first while more than
+// kKwayMaxRuns runs remain), the permutation in w.perm.  Queued on st.
 static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const ull* off_host,
                               ull* off_dev, uint32_t k, const Work& w, const Layout& L,
                               cudaStream_t st, int sms) {
@@ -941,22 +942,47 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
     LEY_TRY(launch("merge_offsets", st, [&] {
         return launch_set_offsets(st, off_dev, off_host, k + 1);
     }));
+    std::vector<ull> off(off_host, off_host + k + 1);  // the runs of the next step, on the host
     int cur = 0;
-    for (uint32_t runs = k; runs > 1; runs = (runs + 1) / 2) {
+    uint32_t runs = k;
+    for (; runs > (uint32_t)kKwayMaxRuns; runs = (runs + 1) / 2) {
         LEY_TRY(launch("merge", st, [&] {
             return launch_merge_round(st, sms * 8, w.tup[cur], w.tup[cur ^ 1], off_dev, runs,
                                       ks.lo_mask);
         }));
         cur ^= 1;
-        if (runs > 2) {
-            // the merged pairs are the runs of the next round
-            LEY_TRY(launch("merge_offsets", st, [&] {
-                return launch_halve_offsets(st, off_dev, runs);
-            }));
-        }
+        // the merged pairs are the runs of the next round
+        LEY_TRY(launch("merge_offsets", st, [&] { return launch_halve_offsets(st, off_dev, runs); }));
+        const uint32_t np = (runs + 1) / 2;
+        for (uint32_t i = 1; i <= np; i++) off[i] = off[std::min<uint32_t>(2 * i, runs)];
+        off.resize(np + 1);
     }
-    LEY_TRY(launch("tuple_index", st, [&] {
-        return launch_tuple_index(st, sms * 4, w.tup[cur], w.perm, m.n);
+    // the sample split table goes to the other tuple buffer
+    const uint32_t step = kway_sample_step(runs);
+    ull S = 0;
+    for (uint32_t i = 0; i < runs; i++) S += (off[i + 1] - off[i] + step - 1) / step;
+    const ull rows_cap = (ull)(L.tup[1] - L.tup[0]) / (4ull * runs);  // u32 rows of `runs`
+    if (S + 1 > rows_cap) {
+        // a merge far smaller than its runs' count (a few records per run):
+        // pairwise rounds to the end
+        for (; runs > 1; runs = (runs + 1) / 2) {
+            LEY_TRY(launch("merge", st, [&] {
+                return launch_merge_round(st, sms * 8, w.tup[cur], w.tup[cur ^ 1], off_dev, runs,
+                                          ks.lo_mask);
+            }));
+            cur ^= 1;
+            if (runs > 2)
+                LEY_TRY(launch("merge_offsets", st, [&] { return launch_halve_offsets(st, off_dev, runs); }));
+        }
+        LEY_TRY(launch("tuple_index", st, [&] {
+            return launch_tuple_index(st, sms * 4, w.tup[cur], w.perm, m.n);
+        }));
+        return LEY_OK;
+    }
+    uint32_t* table = reinterpret_cast<uint32_t*>(w.tup[cur ^ 1]);
+    LEY_TRY(launch("kmerge", st, [&] {
+        return launch_kmerge(st, sms, w.tup[cur], off_dev, runs, (uint32_t)S, ks.lo_mask, table,
+                             rows_cap, w.perm, m.n, w.err);
     }));
     return LEY_OK;
 }

@@ -109,6 +109,17 @@ cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsign
 cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
                                const unsigned long long* off_dev, uint32_t k, uint32_t lo_mask);
 cudaError_t launch_halve_offsets(cudaStream_t s, unsigned long long* off, uint32_t runs);
+// K-way merge path in one pass (k <= kKwayMaxRuns): the sample split table
+// ((S + 1) rows of k u32, S = sum over runs of ceil(len / kway_sample_step(k)))
+// and the tile merges; perm[j] = w of the j-th tuple of the merge of the
+// sorted runs at tup (run r at [off[r], off[r+1]), n tuples in all).
+constexpr int kKwayMaxRuns = 32;
+constexpr int kKwayTile = 4096;
+uint32_t kway_sample_step(uint32_t k);
+cudaError_t launch_kmerge(cudaStream_t st, int sms, const uint4* tup,
+                          const unsigned long long* off_dev, uint32_t k, uint32_t S,
+                          uint32_t lo_mask, uint32_t* table, unsigned long long table_rows,
+                          uint32_t* perm, unsigned long long n, uint32_t* err);
 // dst[0, count) = host[0, count), count <= kMaxOffsets, stream-ordered on s
 // (the values travel in the kernel's parameters).
 constexpr int kMaxOffsets = 129;  // k + 1 offsets of at most 128 runs

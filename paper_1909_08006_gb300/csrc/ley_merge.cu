@@ -1,14 +1,15 @@
-// K-way merge of sorted runs (the merge stage of Section 3.2: "sorted and
-// merged by the merger thread to a globally sorted partition, using a K-way
-// merge algorithm"), done on the GPU as rounds of pairwise merge-path merges
-// (Green, McColl and Bader, "GPU Merge Path", 2012) over 16-byte tuples.
+// K-way merge of sorted runs (the merge stage of Section 3.2: the runs are
+// merged into a globally sorted partition by a K-way merge), done on the GPU
+// over 16-byte tuples by merge path (Green, McColl and Bader, "GPU Merge
+// Path", 2012), generalised to k runs in one pass (below); a fan-in above
+// kKwayMaxRuns is first brought down by rounds of pairwise merges.
 //
 // The k runs lie back to back in one tuple array, run r at [off[r], off[r+1]),
 // each sorted by (key, position).  Positions grow with the run number, so
 // comparing full tuples (key, then position) merges stably: on equal keys the
-// lower run comes first, which is the order of the input.  Round by round,
-// runs 2i and 2i+1 are merged into the other buffer at the same place; an odd
-// last run is copied.  ceil(log2 k) rounds sort the whole array.
+// lower run comes first, which is the order of the input.  In a pairwise
+// round runs 2i and 2i+1 are merged into the other buffer at the same place
+// (an odd last run is copied).
 #define LEY_FILE_ID 3
 #include "ley_kernels.h"
 
@@ -104,6 +105,165 @@ k_merge_round(const uint4* __restrict__ src, uint4* __restrict__ dst, const ull*
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < m; i += kMergeThreads) dst[a0 + d0 + i] = so[i];
     }
+}
+
+// ------------------------------------------------------ k-way merge path
+//
+// One pass over all k runs (k <= kKwayMaxRuns) instead of ceil(log2 k)
+// pairwise rounds.  Every s-th tuple of every run is a sample, with
+// s = kKwayTile / k (at most 256).  For each sample x the split vector
+// split_r(x) = #{y in run r : y < x} is found by k binary searches, and its
+// rank among all samples, q(x) = sum_r ceil(split_r(x) / s), by the same
+// numbers (the samples of run r below x are those at positions below
+// split_r(x)); the vector goes to row q(x) of a table, which is therefore the
+// samples' split vectors in merged order, with the runs' ends as the last
+// row.  The merged output between two consecutive samples holds at most s
+// tuples of the first sample's run and fewer than s of every other run (one
+// more would be a sample in between), so at most kKwayTile tuples: one CTA
+// merges each such tile in shared memory, every tuple's place in the tile
+// being its index in its own run's piece plus its lower bounds in the other
+// pieces, and the tile's first output position the sum of its first row.
+constexpr int kKwayThreads = 256;
+
+__device__ __forceinline__ uint32_t kw_lower_bound(const uint4* a, uint32_t n, const uint4& x,
+                                                   uint32_t lo_mask) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (mtup_less(a[mid], x, lo_mask)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One warp per sample; lane r handles run r.  table has (S + 1) rows of k.
+__global__ void __launch_bounds__(256)
+k_kmerge_samples(const uint4* __restrict__ tup, const ull* __restrict__ off, uint32_t k,
+                 uint32_t s, uint32_t lo_mask, uint32_t* __restrict__ table, ull table_rows,
+                 uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const ull gw = ((ull)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const ull nw = ((ull)gridDim.x * blockDim.x) >> 5;
+    const uint32_t r = (uint32_t)lane;
+    const ull r0 = r < k ? off[r] : 0, r1 = r < k ? off[r + 1] : 0;
+    const uint32_t nr = (uint32_t)(r1 - r0);
+    const uint32_t cr = (nr + s - 1) / s;  // samples of run r
+    uint32_t incl = cr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t cb = incl - cr;  // first sample id of run r
+    const uint32_t S = __shfl_sync(0xffffffffu, incl, 31);
+    if ((ull)S + 1 > table_rows) {  // the host sized the table: never
+        if (gw == 0 && lane == 0) LEY_FAIL(err, kErrCapacity);
+        return;
+    }
+    if (gw == 0 && r < k) table[(ull)S * k + r] = nr;  // the last row: every run's end
+    for (ull sid = gw; sid < S; sid += nw) {
+        // the run of this sample: the highest run whose first sample id is
+        // <= sid (an empty run shares its id with the next run)
+        const uint32_t in_lo = __ballot_sync(0xffffffffu, r < k && cb <= (uint32_t)sid);
+        const int i = 31 - __clz(in_lo);
+        const uint32_t cbi = __shfl_sync(0xffffffffu, cb, i);
+        const ull offi = __shfl_sync(0xffffffffu, r0, i);
+        const uint32_t pos = ((uint32_t)sid - cbi) * s;
+        const uint4 x = tup[offi + pos];
+        uint32_t split = 0;
+        if (r < k) split = r == (uint32_t)i ? pos : kw_lower_bound(tup + r0, nr, x, lo_mask);
+        const uint32_t q = __reduce_add_sync(0xffffffffu, r < k ? (split + s - 1) / s : 0u);
+        if (q >= S) {  // the ranks of the samples are a permutation of [0, S): never
+            if (lane == 0) LEY_FAIL(err, kErrCapacity);
+            continue;
+        }
+        if (r < k) table[(ull)q * k + r] = split;
+    }
+}
+
+// One CTA per tile of consecutive table rows; perm[j] = the w field (the
+// position in the concatenated runs) of the j-th tuple of the merge.
+__global__ void __launch_bounds__(kKwayThreads)
+k_kmerge_tiles(const uint4* __restrict__ tup, const ull* __restrict__ off, uint32_t k,
+               const uint32_t* __restrict__ table, uint32_t S, uint32_t lo_mask,
+               uint32_t* __restrict__ perm, ull n, uint32_t* err) {
+    extern __shared__ uint4 sm[];  // kKwayTile tuples
+    __shared__ uint32_t t_lo[kKwayMaxRuns], pre[kKwayMaxRuns + 1];
+    __shared__ ull t_base, run0[kKwayMaxRuns];
+    const int tid = threadIdx.x;
+    for (uint32_t q = blockIdx.x; q < S; q += gridDim.x) {
+        __syncthreads();  // the previous tile's shared state is no longer read
+        if (tid < (int)k) {
+            const uint32_t a = table[(ull)q * k + tid], b = table[(ull)(q + 1) * k + tid];
+            t_lo[tid] = a;
+            pre[tid + 1] = b >= a ? b - a : 0u;
+            run0[tid] = off[tid];
+            if (b < a) LEY_FAIL(err, kErrCapacity);  // rows out of order: never
+        }
+        __syncthreads();
+        if (tid == 0) {
+            ull base = 0;
+            pre[0] = 0;
+            for (uint32_t r = 0; r < k; r++) {
+                base += t_lo[r];
+                pre[r + 1] += pre[r];
+            }
+            t_base = base;
+        }
+        __syncthreads();
+        const uint32_t total = pre[k];
+        const ull base = t_base;
+        if (total > (uint32_t)kKwayTile || base + total > n) {  // never for a valid table
+            if (tid == 0) LEY_FAIL(err, kErrCapacity);
+            continue;
+        }
+        for (uint32_t f = tid; f < total; f += kKwayThreads) {
+            uint32_t lo = 0, hi = k;  // the run whose piece holds f: pre[r] <= f < pre[r + 1]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pre[mid] <= f) lo = mid;
+                else hi = mid;
+            }
+            sm[f] = tup[run0[lo] + t_lo[lo] + (f - pre[lo])];
+        }
+        __syncthreads();
+        for (uint32_t f = tid; f < total; f += kKwayThreads) {
+            uint32_t a = 0, hi = k;
+            while (hi - a > 1) {
+                const uint32_t mid = (a + hi) >> 1;
+                if (pre[mid] <= f) a = mid;
+                else hi = mid;
+            }
+            const uint4 e = sm[f];
+            uint32_t rank = f - pre[a];
+            for (uint32_t r = 0; r < k; r++)
+                if (r != a) rank += kw_lower_bound(sm + pre[r], pre[r + 1] - pre[r], e, lo_mask);
+            if (rank < total) perm[base + rank] = e.w;
+            else LEY_FAIL(err, kErrCapacity);  // inconsistent order: never
+        }
+    }
+}
+
+uint32_t kway_sample_step(uint32_t k) {
+    const uint32_t s = (uint32_t)kKwayTile / (k ? k : 1);
+    return s > 256 ? 256 : s;
+}
+
+cudaError_t launch_kmerge(cudaStream_t st, int sms, const uint4* tup, const ull* off_dev,
+                          uint32_t k, uint32_t S, uint32_t lo_mask, uint32_t* table,
+                          ull table_rows, uint32_t* perm, ull n, uint32_t* err) {
+    const uint32_t s = kway_sample_step(k);
+    const int sgrid = (int)min((ull)sms * 8, ((ull)S * 32 + 255) / 256 + 1);
+    k_kmerge_samples<<<sgrid, 256, 0, st>>>(tup, off_dev, k, s, lo_mask, table, table_rows, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || S == 0) return e;
+    e = cudaFuncSetAttribute(k_kmerge_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kKwayTile * sizeof(uint4)));
+    if (e != cudaSuccess) return e;
+    const int tgrid = (int)min((ull)sms * 3, (ull)S);
+    k_kmerge_tiles<<<tgrid, kKwayThreads, kKwayTile * sizeof(uint4), st>>>(
+        tup, off_dev, k, table, S, lo_mask, perm, n, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,

@@ -143,12 +143,20 @@ def test_external_budget_too_small(ley):
     assert e.value.status == ley.LEY_ENOMEM
 
 
-@pytest.mark.parametrize("k,alpha", [(1, None), (2, None), (3, b"AB"), (8, None), (17, b"xyz"),
-                                     (5, b"Q")])
-def test_merge_records_matches_oracle(orc, ley, k, alpha):
+@pytest.mark.parametrize("k,alpha,base,step", [
+    (1, None, 1000, 777), (2, None, 1000, 777), (3, b"AB", 1000, 777), (8, None, 1000, 777),
+    (17, b"xyz", 1000, 777), (5, b"Q", 1000, 777),
+    (16, None, 30_000, 5_001),   # the external sort's fan-in, tiles of up to 4096 tuples
+    (32, b"AB", 2000, 301),      # the largest one-pass fan-in, ties across every run
+    (33, None, 1500, 97),        # one pairwise round first, then the one-pass merge
+    (128, b"xy", 300, 41),       # the largest fan-in: two pairwise rounds first
+    (32, None, 3, 1),            # a few records per run, one sample each
+    (32, None, 1, 0),            # one record per run: too small for the table, pairwise only
+])
+def test_merge_records_matches_oracle(orc, ley, k, alpha, base, step):
     runs, starts = [], [0]
     for r in range(k):
-        m = 0 if r == 1 else 1000 + 777 * r
+        m = 0 if r == 1 else base + step * r
         a = datagen.uniform_records(m, seed=50 + r).numpy().copy()
         if alpha is not None:
             al = np.frombuffer(bytes(alpha), dtype=np.uint8)
