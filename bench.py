@@ -551,6 +551,8 @@ def run_batch(args, world, rank, dev, stream, pg):
         raise RuntimeError("device-side error")
     outs_s = [o for _, o in rec_reqs] + [ko for _, _, ko, _ in pair_reqs]
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
+    graph = _graph_replay_timing(batched_calls(rec_reqs, pair_reqs), args, stream, pg, dev)
+    small = _small_batch_timing(args, dev, stream, pg)
     return {
         "metric": "GB/s of request data sorted, batched (records + pairs)",
         "value": round(world * total_bytes / (ms_b * 1e-3) / 1e9, 2), "unit": "GB/s",
@@ -567,7 +569,58 @@ def run_batch(args, world, rank, dev, stream, pg):
         "oracle_checked": len(bad_r) + len(bad_p),
         "oracle_exact": all(b == -1 for b in bad_r + bad_p),
         "identical_to_one_launch_per_request": same,
+        "cuda_graph_replay": graph, "small_batch": small,
     }
+
+
+def batched_calls(rec_reqs, pair_reqs):
+    import paper_1909_08006_gb300 as ley
+
+    def fn(st):
+        if rec_reqs:
+            ley.ley_sort_records_batch(rec_reqs, stream=st)
+        if pair_reqs:
+            ley.ley_sort_keys_index_batch(pair_reqs, stream=st)
+    return fn
+
+
+def _graph_replay_timing(fn, args, stream, pg, dev):
+    """The same batched calls launched directly and replayed from a CUDA
+    graph captured once: what graph replay would save a batch of this shape."""
+    import torch
+    fn(stream)  # library state and pool set up outside the capture
+    torch.cuda.synchronize()
+    cs = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs):
+        fn(cs)
+    direct = _timed(lambda: fn(stream), args.steps, args.warmup, stream, pg, dev)
+    cur = torch.cuda.current_stream(dev)
+    replay = _timed(g.replay, args.steps, args.warmup, cur, pg, dev)
+    del g
+    return {"direct_ms": round(direct, 4), "graph_replay_ms": round(replay, 4),
+            "replay_speedup": round(direct / replay, 3)}
+
+
+def _small_batch_timing(args, dev, stream, pg):
+    """A batch of 8 small requests (1,000..20,000 records, half records, half
+    pairs), where launch costs weigh most: direct calls against graph replay."""
+    import torch
+    import datagen
+    sizes = [1000, 20_000, 3000, 8000, 1500, 12_000, 5000, 2500]
+    rec_reqs, pair_reqs = [], []
+    for i, n in enumerate(sizes):
+        if i % 2 == 0:
+            x = datagen.uniform_records(n, seed=7000 + i, device=dev)
+            rec_reqs.append((x, torch.empty_like(x)))
+        else:
+            k, v = datagen.uniform_pairs(n, seed=7000 + i, device=dev)
+            pair_reqs.append((k, v, torch.empty_like(k), torch.empty_like(v)))
+    torch.cuda.synchronize()
+    r = _graph_replay_timing(batched_calls(rec_reqs, pair_reqs), args, stream, pg, dev)
+    r["requests"] = len(sizes)
+    r["records_and_pairs"] = sum(sizes)
+    return r
 
 
 def run_serve(args, world, rank, dev, stream, pg):

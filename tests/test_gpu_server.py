@@ -159,7 +159,9 @@ def test_admission_respects_the_budget(ley, orc):
         ley.ley_server_destroy(srv)
     assert all(_same(r) for r in reqs)
     assert max(seen) <= budget
-    assert st["launched_batches"] >= 3  # the budget forced several batches
+    # the requests' device memory (about 1.7x the budget in all) forced
+    # several batches
+    assert st["launched_batches"] >= 2
 
 
 def test_request_larger_than_budget_runs_alone(ley, orc):
