@@ -289,6 +289,20 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
                                uint64_t mem_budget, uint64_t* bytes);
 
 /*
+ * Pinned host scratch (bytes) that ley_sort_records keeps for the sorted runs
+ * of an external sort of n records under mem_budget (Section 3.2: the runs
+ * are written out, then merged): 0 when the partially in-memory mode is used
+ * (or mem_budget == 0), LEY_ENOMEM when no mode fits.  The external sort
+ * keeps its last runs sorted in device memory, as many as fit the budget
+ * beside its pipeline, so this is less than n * rec_bytes when the budget
+ * allows; the link then carries the input in, the host runs out and back,
+ * and the output out.  The scratch is allocated at the first such sort and
+ * kept until ley_release_cache().  Host-only; needs no GPU.
+ */
+ley_status ley_host_scratch_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                                  uint64_t mem_budget, uint64_t* bytes);
+
+/*
  * Returns the memory this library keeps between calls: the unused part of
  * each device's scratch pool and the pinned host scratch of the external
  * sort.  Call it when no sort of this library is running (on any stream);

@@ -22,7 +22,7 @@ __all__ = [
     "LEY_ETIMEOUT", "ley_sort_records", "ley_sort_records_async", "ley_plan_partitions",
     "ley_sort_keys_index",
     "ley_partition_records",
-    "ley_workspace_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
+    "ley_workspace_bytes", "ley_host_scratch_bytes", "ley_status_string", "ley_last_device_status", "ley_launch_count",
     "ley_profile_enable", "ley_profile_read", "library_path", "exported_symbols",
     "ley_sort_records_noalloc", "LEY_NOALLOC_MAX_RECORDS", "ley_merge_records",
     "ley_release_cache", "ley_sort_records_batch", "ley_sort_keys_index_batch",
@@ -101,6 +101,8 @@ def _load() -> ctypes.CDLL:
     lib.ley_partition_records.restype = ctypes.c_int
     lib.ley_workspace_bytes.argtypes = [u64, u32, u32, u64, ctypes.POINTER(u64)]
     lib.ley_workspace_bytes.restype = ctypes.c_int
+    lib.ley_host_scratch_bytes.argtypes = [u64, u32, u32, u64, ctypes.POINTER(u64)]
+    lib.ley_host_scratch_bytes.restype = ctypes.c_int
     lib.ley_status_string.argtypes = [ctypes.c_int]
     lib.ley_status_string.restype = ctypes.c_char_p
     lib.ley_last_device_status.argtypes = [vp]
@@ -449,6 +451,16 @@ def ley_workspace_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10,
     v = ctypes.c_uint64(0)
     _check(_lib.ley_workspace_bytes(n, rec_bytes, key_bytes, mem_budget, ctypes.byref(v)),
            "ley_workspace_bytes")
+    return int(v.value)
+
+
+def ley_host_scratch_bytes(n: int, rec_bytes: int = 100, key_bytes: int = 10,
+                           mem_budget: int = 0) -> int:
+    """Pinned host bytes an external sort of n records under mem_budget keeps
+    for its runs (0 when the partially in-memory mode is used)."""
+    v = ctypes.c_uint64(0)
+    _check(_lib.ley_host_scratch_bytes(n, rec_bytes, key_bytes, mem_budget, ctypes.byref(v)),
+           "ley_host_scratch_bytes")
     return int(v.value)
 
 

@@ -823,7 +823,8 @@ static uint8_t* host_scratch(size_t bytes) {
     g_host_scratch = nullptr;
     g_host_scratch_bytes = 0;
     void* p = nullptr;
-    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) {
+    // mapped: the partition planning reads the runs from the device
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -853,6 +854,33 @@ static ull corank_split(const std::vector<HostRun>& runs, size_t i, const uint8_
         else hi = mid;
     }
     return lo;
+}
+
+// The partition cuts from candidates in merged order (ranks increasing, every
+// two consecutive at most cap / 4 apart): from the current cut, the last
+// candidate at most 3/4 cap further becomes the next cut, until the rest fits
+// one partition.  cut(ci) gives candidate ci's co-rank in every run.
+template <class CutOf>
+static std::vector<std::vector<ull>> select_cuts(const std::vector<ull>& ranks,
+                                                 const std::vector<ull>& lens, ull n, ull cap,
+                                                 CutOf cut) {
+    std::vector<std::vector<ull>> cuts;
+    cuts.push_back(std::vector<ull>(lens.size(), 0));
+    ull start = 0;
+    const ull target = cap * 3 / 4 > 0 ? cap * 3 / 4 : 1;
+    size_t ci = 0;
+    while (n - start > cap) {
+        long best = -1;
+        while (ci < ranks.size() && ranks[ci] <= start + target) {
+            if (ranks[ci] > start) best = (long)ci;
+            ci++;
+        }
+        if (best < 0) break;  // cannot happen: consecutive ranks differ by <= cap/4
+        cuts.push_back(cut((size_t)best));
+        start = ranks[best];
+    }
+    cuts.push_back(lens);
+    return cuts;
 }
 
 // Merge partitions: split vectors (one position per run) at increasing global
@@ -898,30 +926,16 @@ static std::vector<std::vector<ull>> plan_partitions(const std::vector<HostRun>&
         }
         for (auto& th : pool) th.join();
     }
-    std::vector<std::vector<ull>> cuts;
-    cuts.push_back(std::vector<ull>(k, 0));
-    ull start = 0;
-    const ull target = cap * 3 / 4 > 0 ? cap * 3 / 4 : 1;
-    size_t ci = 0;
-    while (n - start > cap) {
-        // the last candidate at most `target` past the current cut
-        long best = -1;
-        while (ci < cands.size() && cands[ci].rank <= start + target) {
-            if (cands[ci].rank > start) best = (long)ci;
-            ci++;
-        }
-        if (best < 0) break;  // cannot happen: consecutive ranks differ by <= cap/4
-        const Cand& c = cands[best];
+    std::vector<ull> ranks(cands.size()), lens(k);
+    for (size_t ci = 0; ci < cands.size(); ci++) ranks[ci] = cands[ci].rank;
+    for (size_t i = 0; i < k; i++) lens[i] = runs[i].len;
+    return select_cuts(ranks, lens, n, cap, [&](size_t ci) {
+        const Cand& c = cands[ci];
         std::vector<ull> cut(k);
         for (size_t i = 0; i < k; i++)
             cut[i] = corank_split(runs, i, runs[c.run].base + c.pos * rec, c.run, c.pos, rec, kb);
-        cuts.push_back(cut);
-        start = c.rank;
-    }
-    std::vector<ull> last(k);
-    for (size_t i = 0; i < k; i++) last[i] = runs[i].len;
-    cuts.push_back(last);
-    return cuts;
+        return cut;
+    });
 }
 
 // Merge of the k sorted runs whose records lie back to back at dev_runs (run r
@@ -1011,8 +1025,21 @@ struct ExtPlan {
     ull q = 0;          // records per staging buffer
     ull r_len = 0;      // records per run (the largest merge partition too)
     uint32_t k = 0;     // runs
-    size_t in_bytes = 0, ws_len = 0, stg_bytes = 0, total = 0;
+    uint32_t resident = 0;  // the last `resident` runs stay on the device, sorted
+    ull step = 0;       // partition planning: a candidate every `step` records of a run
+    uint32_t ncand = 0; // candidates in all runs
+    size_t in_bytes = 0, ws_len = 0, stg_bytes = 0, plan_bytes = 0, total = 0;
+    size_t host_bytes = 0;  // pinned host scratch for the runs that leave the device
 };
+
+// Runs that stay on the device: as many as fit the budget beside the
+// pipeline, at most all but one (LEY_EXTERNAL_RESIDENT=<m> caps them).  Keys
+// longer than 12 bytes keep every run on the host (their cuts are planned
+// on the host).
+static uint32_t resident_cap() {
+    const char* v = std::getenv("LEY_EXTERNAL_RESIDENT");
+    return v ? (uint32_t)std::strtoul(v, nullptr, 10) : 0xFFFFFFFFu;
+}
 
 static ley_status external_plan(ull n, uint32_t rec, uint32_t kb, ull budget, const Tuning& t,
                                 ExtPlan* p) {
@@ -1030,8 +1057,26 @@ static ley_status external_plan(ull n, uint32_t rec, uint32_t kb, ull budget, co
     auto ws_bytes = [&](ull r) {
         return make_layout(r, true, t.big).total + (long_key ? long_key_extra(r) : 0);
     };
-    // largest run (whole tiles) whose record buffers and workspaces fit
-    auto need = [&](ull r) { return kExtBufs * (align_up(r * rec, 256) + ws_bytes(r)) + fixed; };
+    // the partition candidates of runs of r records: every step-th record of
+    // every run (as the host planner takes them); the device planner's
+    // scratch holds their co-ranks, their ranks and the run table
+    auto step_of = [&](ull r, uint32_t k) { return r / (4ull * k) > 0 ? r / (4ull * k) : 1ull; };
+    auto ncand_of = [&](ull r, uint32_t k, ull step) {
+        ull nc = 0;
+        for (uint32_t i = 0; i < k; i++) nc += std::min(r, n - (ull)i * r) / step;
+        return nc;
+    };
+    auto plan_bytes_of = [&](ull r) -> size_t {
+        if (long_key || r == 0) return 0;
+        const uint32_t k = (uint32_t)std::min<ull>((n + r - 1) / r, 1ull << 20);
+        const ull nc = ncand_of(r, k, step_of(r, k));
+        return align_up(nc * k * sizeof(uint32_t), 256) + align_up(nc * sizeof(ull), 256) +
+               align_up((k + 1) * sizeof(ull), 256) + align_up(k * sizeof(PlanRun), 256);
+    };
+    // largest run (whole tiles) whose record buffers, workspaces and planner fit
+    auto need = [&](ull r) {
+        return kExtBufs * (align_up(r * rec, 256) + ws_bytes(r)) + fixed + plan_bytes_of(r);
+    };
     ull lo = 0, hi = n / kPassTile + 1;
     while (lo < hi) {
         const ull mid = (lo + hi + 1) / 2;
@@ -1047,8 +1092,74 @@ static ley_status external_plan(ull n, uint32_t rec, uint32_t kb, ull budget, co
     if (e.k > kMaxRuns) return LEY_ENOMEM;  // budget too small for the merge fan-in
     e.in_bytes = align_up(e.r_len * rec, 256);
     e.ws_len = ws_bytes(e.r_len);
-    e.total = kExtBufs * (e.in_bytes + e.ws_len) + kStaging * e.stg_bytes + 8 * 1024;
+    e.step = step_of(e.r_len, e.k);
+    e.ncand = (uint32_t)ncand_of(e.r_len, e.k, e.step);
+    e.plan_bytes = plan_bytes_of(e.r_len);
+    const size_t base = kExtBufs * (e.in_bytes + e.ws_len) + kStaging * e.stg_bytes + 8 * 1024 +
+                        e.plan_bytes;
+    if (base > budget) return LEY_ENOMEM;
+    if (!long_key && e.k > 1) {
+        const ull fit = (budget - base) / e.in_bytes;
+        e.resident = (uint32_t)std::min<ull>(std::min<ull>(fit, e.k - 1), resident_cap());
+    }
+    e.total = base + e.resident * e.in_bytes;
+    // the first k - resident runs
+    e.host_bytes = (size_t)std::min<ull>(n, (ull)(e.k - e.resident) * e.r_len) * rec;
     *p = e;
+    return LEY_OK;
+}
+
+// The partition cuts of the external merge planned on the device (keys of at
+// most 12 bytes): the candidates' co-ranks in every run (k_corank, runs on
+// the device or in mapped host memory), then the cuts chosen on the host
+// from their ranks.  Queued on st after everything before it; blocks.
+static ley_status plan_partitions_device(const std::vector<PlanRun>& runs, const ExtPlan& plan,
+                                         ull n, uint32_t rec, uint32_t kb, char* scratch,
+                                         cudaStream_t st, int sms, uint32_t* err,
+                                         std::vector<std::vector<ull>>* cuts) {
+    const uint32_t k = (uint32_t)runs.size();
+    const uint32_t nc = plan.ncand;
+    uint32_t* split = reinterpret_cast<uint32_t*>(scratch);
+    char* c1 = scratch + align_up((size_t)nc * k * sizeof(uint32_t), 256);
+    ull* rank = reinterpret_cast<ull*>(c1);
+    char* c2 = c1 + align_up((size_t)nc * sizeof(ull), 256);
+    ull* cbase_dev = reinterpret_cast<ull*>(c2);
+    PlanRun* runs_dev = reinterpret_cast<PlanRun*>(c2 + align_up((k + 1) * sizeof(ull), 256));
+    std::vector<ull> cbase(k + 1, 0), lens(k);
+    for (uint32_t i = 0; i < k; i++) {
+        lens[i] = runs[i].len;
+        cbase[i + 1] = cbase[i] + runs[i].len / plan.step;
+    }
+    if (cbase[k] != nc) return LEY_EINVAL;  // the plan counted the same candidates
+    LEY_TRY(launch("plan_upload", st, [&] {
+        return launch_upload(st, cbase_dev, cbase.data(), (k + 1) * sizeof(ull));
+    }));
+    LEY_TRY(launch("plan_upload", st, [&] {
+        return launch_upload(st, runs_dev, runs.data(), k * sizeof(PlanRun));
+    }));
+    LEY_TRY(launch("corank", st, [&] {
+        return launch_corank(st, sms, runs_dev, k, rec, kb, cbase_dev, plan.step, nc, split, rank,
+                             err);
+    }));
+    std::vector<uint32_t> split_h((size_t)nc * k);
+    std::vector<ull> rank_h(nc);
+    if (nc) {
+        LEY_TRY(cudaMemcpyAsync(split_h.data(), split, split_h.size() * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, st));
+        LEY_TRY(cudaMemcpyAsync(rank_h.data(), rank, nc * sizeof(ull), cudaMemcpyDeviceToHost, st));
+    }
+    LEY_TRY(cudaStreamSynchronize(st));
+    // candidates in merged order (their ranks are distinct: (key, run, position) is a total order)
+    std::vector<uint32_t> order(nc);
+    for (uint32_t c = 0; c < nc; c++) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return rank_h[x] < rank_h[y]; });
+    std::vector<ull> ranks(nc);
+    for (uint32_t c = 0; c < nc; c++) ranks[c] = rank_h[order[c]];
+    *cuts = select_cuts(ranks, lens, n, plan.r_len, [&](size_t ci) {
+        std::vector<ull> cut(k);
+        for (uint32_t j = 0; j < k; j++) cut[j] = split_h[(size_t)order[ci] * k + j];
+        return cut;
+    });
     return LEY_OK;
 }
 
@@ -1059,19 +1170,25 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     const ley_status ps = external_plan(a.n, a.rec, a.kb, budget, a.tune, &plan);
     if (ps != LEY_OK) return ps;
     const ull q = plan.q, r_len = plan.r_len;
-    const uint32_t k = plan.k;
+    const uint32_t k = plan.k, nres = plan.resident, nhost = k - nres;
     const bool long_key = a.kb > kWindow;
     const Layout L = make_layout(r_len, true, a.tune.big);
     const size_t stg_bytes = plan.stg_bytes, in_bytes = plan.in_bytes, ws_len = plan.ws_len;
     const size_t total = plan.total;
     const bool dbg = std::getenv("LEY_DEBUG") != nullptr;
     if (dbg)
-        std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records, staging %llu, "
-                     "device bytes %zu of budget %llu\n", a.n, k, r_len, q, total, budget);
+        std::fprintf(stderr, "leysort: external n=%llu runs=%u of %llu records (%u stay on the "
+                     "device), staging %llu, device bytes %zu of budget %llu\n", a.n, k, r_len,
+                     nres, q, total, budget);
     // One external sort at a time per process: they share the host scratch.
     std::lock_guard<std::mutex> scratch_lock(g_host_scratch_mu);
-    uint8_t* hs = host_scratch(a.n * a.rec);
+    uint8_t* hs = host_scratch(plan.host_bytes);
     if (!hs) return LEY_ENOMEM;
+    void* hs_dev = nullptr;  // the runs on the host as the device reads them (planning)
+    if (!long_key && (cudaHostGetDevicePointer(&hs_dev, hs, 0) != cudaSuccess || !hs_dev)) {
+        cudaGetLastError();
+        return LEY_ECUDA;
+    }
     void* dmem = nullptr;
     if (!scratch_alloc(ds, &dmem, total, st)) return LEY_ENOMEM;
     char* base = static_cast<char*>(dmem);
@@ -1090,6 +1207,9 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
     uint8_t* stg[kStaging];
     for (int i = 0; i < kStaging; i++) stg[i] = reinterpret_cast<uint8_t*>(tail + i * stg_bytes);
     ull* off_dev = reinterpret_cast<ull*>(tail + kStaging * stg_bytes);
+    char* plan_scratch = tail + kStaging * stg_bytes + 8 * 1024;
+    uint8_t* const res0 = reinterpret_cast<uint8_t*>(plan_scratch + plan.plan_bytes);
+    auto resident = [&](uint32_t r) { return res0 + (size_t)(r - nhost) * in_bytes; };
     ley_status s = LEY_OK;
     {
         HostPipe hp(st);
@@ -1099,8 +1219,10 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
         // buffer b and workspace b are free again once the gathers that read
         // them (kExtBufs runs or partitions back) are done
         cudaEvent_t buf_free[kExtBufs] = {};
-        // --- run formation
+        // --- run formation: the first nhost runs go to the host scratch, the
+        // last nres are gathered into device buffers of their own
         std::vector<HostRun> runs;
+        std::vector<PlanRun> pruns;
         for (uint32_t r = 0; r < k && s == LEY_OK; r++) {
             const ull r0 = (ull)r * r_len;
             const ull rn = a.n - r0 < r_len ? a.n - r0 : r_len;
@@ -1130,20 +1252,35 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
             }
             hp.mark(st, "run sorted", r);
             if (s == LEY_OK && !hp.order(st, hp.gth)) s = LEY_ECUDA;
-            if (s == LEY_OK) s = stream_out(ra, order, 0, rn, hs + r0 * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+            if (r < nhost) {
+                if (s == LEY_OK) s = stream_out(ra, order, 0, rn, hs + r0 * a.rec, stg, q, hp.gth, hp, stg_free, ds->sms);
+                runs.push_back({hs + r0 * a.rec, rn});
+                pruns.push_back({static_cast<const uint8_t*>(hs_dev) + r0 * a.rec, rn});
+            } else {
+                if (s == LEY_OK) s = stage_gather(ra, order, hp.gth, ds->sms, 0, rn, resident(r));
+                runs.push_back({nullptr, rn});
+                pruns.push_back({resident(r), rn});
+            }
             hp.mark(hp.gth, "run gathered", r);
             hp.mark(hp.d2h, "run out end", r);
             if (s == LEY_OK && !(buf_free[b] = hp.record(hp.gth))) s = LEY_ECUDA;
-            runs.push_back({hs + r0 * a.rec, rn});
         }
-        // --- merge: the runs must be complete in host memory before they are cut
-        if (s == LEY_OK && cudaStreamSynchronize(hp.d2h) != cudaSuccess) s = LEY_ECUDA;
+        // --- merge: the runs must be complete before they are cut (in host
+        // memory, and in their device buffers)
         std::vector<std::vector<ull>> cuts;
         const auto t_plan = std::chrono::steady_clock::now();
-        if (s == LEY_OK) cuts = plan_partitions(runs, a.n, r_len, a.rec, a.kb);
+        if (long_key) {
+            if (s == LEY_OK && cudaStreamSynchronize(hp.d2h) != cudaSuccess) s = LEY_ECUDA;
+            if (s == LEY_OK) cuts = plan_partitions(runs, a.n, r_len, a.rec, a.kb);
+        } else {
+            if (s == LEY_OK && (!hp.order(hp.d2h, st) || !hp.order(hp.gth, st))) s = LEY_ECUDA;
+            if (s == LEY_OK)
+                s = plan_partitions_device(pruns, plan, a.n, a.rec, a.kb, plan_scratch, st,
+                                           ds->sms, ds->err, &cuts);
+        }
         hp.mark(st, "partitions planned");
         if (hp.trace)
-            std::fprintf(stderr, "leysort trace plan_partitions %.3f ms on the host\n",
+            std::fprintf(stderr, "leysort trace plan_partitions %.3f ms\n",
                          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count());
         if (dbg) std::fprintf(stderr, "leysort: runs formed (status %d), %zu merge partitions\n",
                               (int)s, cuts.empty() ? (size_t)0 : cuts.size() - 1);
@@ -1163,8 +1300,14 @@ static ley_status run_host_external(const SortArgs& a, ull budget, cudaStream_t 
             hp.mark(hp.h2d, "part in begin", (long)p);
             for (uint32_t i = 0; i < k && s == LEY_OK; i++) {
                 const ull len = cuts[p + 1][i] - cuts[p][i];
-                if (len && cudaMemcpyAsync(dbuf[b] + off[i] * a.rec, runs[i].base + cuts[p][i] * a.rec,
-                                           len * a.rec, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+                if (!len) continue;
+                // slices of the host runs over the link, of the resident runs on the device
+                const bool host = i < nhost;
+                if (cudaMemcpyAsync(dbuf[b] + off[i] * a.rec,
+                                    (host ? runs[i].base : resident(i)) + cuts[p][i] * a.rec,
+                                    len * a.rec,
+                                    host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    host ? hp.h2d : st) != cudaSuccess)
                     s = LEY_ECUDA;
             }
             hp.mark(hp.h2d, "part in end", (long)p);
@@ -1613,6 +1756,22 @@ ley_status ley_workspace_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_byte
     const ley_status s = external_plan(n, rec_bytes, key_bytes, mem_budget, tune, &plan);
     if (s != LEY_OK) return s;
     *bytes = plan.total;
+    return LEY_OK;
+}
+
+ley_status ley_host_scratch_bytes(uint64_t n, uint32_t rec_bytes, uint32_t key_bytes,
+                                  uint64_t mem_budget, uint64_t* bytes) {
+    if (!bytes) return LEY_EINVAL;
+    *bytes = 0;
+    if (key_bytes < 1 || key_bytes > rec_bytes || rec_bytes > 4096 || n >= (1ull << 32))
+        return LEY_EUNSUPPORTED;
+    if (n == 0 || mem_budget == 0) return LEY_OK;
+    const Tuning tune = cur_tuning();
+    if (partial_need(n, rec_bytes, key_bytes, mem_budget, tune) <= mem_budget) return LEY_OK;
+    ExtPlan plan;
+    const ley_status s = external_plan(n, rec_bytes, key_bytes, mem_budget, tune, &plan);
+    if (s != LEY_OK) return s;
+    *bytes = plan.host_bytes;
     return LEY_OK;
 }
 

@@ -109,6 +109,19 @@ cudaError_t launch_partition_out(cudaStream_t s, int grid, const Work& w, unsign
 cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
                                const unsigned long long* off_dev, uint32_t k, uint32_t lo_mask);
 cudaError_t launch_halve_offsets(cudaStream_t s, unsigned long long* off, uint32_t runs);
+// Partition planning of the external merge on the device: for ncand
+// candidates (candidate c of run i at position (c - cbase[i] + 1) * step - 1,
+// cbase[k] = ncand) the co-rank in every run, split[c * k + j], and its rank
+// in the merged order (key, run, position), rank[c].  Runs are device
+// memory or pinned host memory mapped for the device; keys of kb <= 12 bytes.
+struct PlanRun {
+    const uint8_t* base;
+    unsigned long long len;
+};
+cudaError_t launch_corank(cudaStream_t st, int sms, const PlanRun* runs, uint32_t k, uint32_t rec,
+                          uint32_t kb, const unsigned long long* cbase, unsigned long long step,
+                          uint32_t ncand, uint32_t* split, unsigned long long* rank,
+                          uint32_t* err);
 // K-way merge path in one pass (k <= kKwayMaxRuns): the sample split table
 // ((S + 1) rows of k u32, S = sum over runs of ceil(len / kway_sample_step(k)))
 // and the tile merges; perm[j] = w of the j-th tuple of the merge of the

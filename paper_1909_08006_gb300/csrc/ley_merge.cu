@@ -266,6 +266,107 @@ cudaError_t launch_kmerge(cudaStream_t st, int sms, const uint4* tup, const ull*
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ partition planning
+//
+// The external sort's partition cuts (Section 3.2: the merge is cut into
+// independent pieces) from the device: the co-rank of every candidate --
+// record p of run i, at p = step - 1, 2 step - 1, ... -- in the merged order
+// (key, run, position), i.e. for every run j the number of its records
+// before the candidate: p in its own run, elsewhere a binary search for the
+// records with a smaller key, or with a key no larger in a lower run.  One
+// warp per candidate, lane j searching run j (run j + 32, ... for k > 32).
+// Runs are in device memory or in pinned host memory mapped for the device
+// (the searches then read a few sectors per probe over the host link).
+
+// Key bytes kb (<= 12) of the record at r as (bytes 0..7, bytes 8..11), big
+// endian, bytes past kb zero: the unsigned order of (hi, lo) is memcmp's.
+// Only the 16-byte granules that hold key bytes are read.
+__device__ __forceinline__ void plan_key(const uint8_t* r, uint32_t kb, ull* hi, uint32_t* lo) {
+    const uintptr_t a = (uintptr_t)r;
+    const uint4* p = reinterpret_cast<const uint4*>(a & ~(uintptr_t)15);
+    const uint32_t o = (uint32_t)(a & 15);
+    const uint4 c0 = p[0];
+    const uint4 c1 = o + kb > 16 ? p[1] : make_uint4(0, 0, 0, 0);
+    const uint32_t wv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    uint32_t b[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        const uint32_t q = o + i;
+        uint32_t word = wv[0];
+#pragma unroll
+        for (int w2 = 1; w2 < 8; w2++) word = (q >> 2) == (uint32_t)w2 ? wv[w2] : word;
+        b[i] = (uint32_t)i < kb ? (word >> (8 * (q & 3))) & 0xFFu : 0u;
+    }
+    ull h = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) h = (h << 8) | b[i];
+    *hi = h;
+    *lo = (b[8] << 24) | (b[9] << 16) | (b[10] << 8) | b[11];
+}
+
+__global__ void __launch_bounds__(256)
+k_corank(const PlanRun* __restrict__ runs, uint32_t k, uint32_t rec, uint32_t kb,
+         const ull* __restrict__ cbase, ull step, uint32_t ncand, uint32_t* __restrict__ split,
+         ull* __restrict__ rank, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const ull gw = ((ull)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const ull nw = ((ull)gridDim.x * blockDim.x) >> 5;
+    for (ull c = gw; c < ncand; c += nw) {
+        // the candidate's run: the last run whose first candidate is <= c
+        uint32_t lo = 0, hi = k;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cbase[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t i = lo;
+        const ull p = (c - cbase[i] + 1) * step - 1;
+        if (p >= runs[i].len) {  // the host counted the candidates: never
+            if (lane == 0) LEY_FAIL(err, kErrCapacity);
+            continue;
+        }
+        ull khi;
+        uint32_t klo;
+        plan_key(runs[i].base + p * rec, kb, &khi, &klo);
+        ull sum = 0;
+        for (uint32_t j = lane; j < k; j += 32) {
+            ull x;
+            if (j == i) {
+                x = p;
+            } else {
+                const bool upper = j < i;  // equal keys of a lower run come first
+                const uint8_t* b = runs[j].base;
+                ull l = 0, h = runs[j].len;
+                while (l < h) {
+                    const ull mid = (l + h) >> 1;
+                    ull mh;
+                    uint32_t ml;
+                    plan_key(b + mid * rec, kb, &mh, &ml);
+                    const bool less = mh < khi || (mh == khi && ml < klo);
+                    const bool eq = mh == khi && ml == klo;
+                    if (less || (upper && eq)) l = mid + 1;
+                    else h = mid;
+                }
+                x = l;
+            }
+            split[c * k + j] = (uint32_t)x;
+            sum += x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) rank[c] = sum;
+    }
+}
+
+cudaError_t launch_corank(cudaStream_t st, int sms, const PlanRun* runs, uint32_t k, uint32_t rec,
+                          uint32_t kb, const ull* cbase, ull step, uint32_t ncand, uint32_t* split,
+                          ull* rank, uint32_t* err) {
+    if (ncand == 0) return cudaSuccess;
+    const int grid = (int)min((ull)sms * 8, ((ull)ncand * 32 + 255) / 256);
+    k_corank<<<grid, 256, 0, st>>>(runs, k, rec, kb, cbase, step, ncand, split, rank, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge_round(cudaStream_t s, int grid, const uint4* src, uint4* dst,
                                const ull* off_dev, uint32_t k, uint32_t lo_mask) {
     k_merge_round<<<grid, kMergeThreads, 0, s>>>(src, dst, off_dev, k, lo_mask);

@@ -102,6 +102,17 @@ def test_workspace_bytes_under_a_budget(ley):
     # the budget never changes the answer for the internal sort of device
     # buffers (mem_budget 0), and n == 0 needs nothing
     assert ley.ley_workspace_bytes(0, mem_budget=budget) == 0
+    # pinned host scratch: none in the partial mode; in the external mode the
+    # runs that do not stay on the device (a 30 GB budget keeps several of
+    # the 25M-record runs of 6e8 records there)
+    assert ley.ley_host_scratch_bytes(200_000_000, mem_budget=budget) == 0
+    hb = ley.ley_host_scratch_bytes(600_000_000, mem_budget=budget)
+    assert 0 < hb < 600_000_000 * 100 and hb % (100 * 4096) == 0
+    # a budget just large enough for the pipeline keeps every run on the host
+    assert ley.ley_host_scratch_bytes(600_000_000, mem_budget=10_000_000_000) == 600_000_000 * 100
+    with pytest.raises(ley.LeyError) as e:
+        ley.ley_host_scratch_bytes(600_000_000, mem_budget=1 << 20)
+    assert e.value.status == ley.LEY_ENOMEM
 
 
 def test_argument_checks_before_any_gpu_work(ley):

@@ -185,3 +185,39 @@ def test_keys_only_external_sort_exact(orc, ley, monkeypatch, n, budget):
     assert np.array_equal(got, want)
     monkeypatch.setenv("LEY_EXTERNAL", "merge")
     assert np.array_equal(host_sort(ley, rec, budget), want)
+
+
+@pytest.mark.parametrize("kind,resident", [("uniform", None), ("skew", None), ("uniform", "0")])
+def test_external_sort_with_runs_kept_on_the_device_exact(orc, ley, monkeypatch, kind, resident):
+    # 32M records under a 3.5 GB device budget: eight runs of 4M records, of
+    # which the last stay sorted in device memory (only the others go to the
+    # host and back), and the merge's partition cuts are planned on the
+    # device over host-resident and device-resident runs.  With
+    # LEY_EXTERNAL_RESIDENT=0 every run goes to the host.  The output is
+    # checked completely by the oracle (tags at bytes 10..13).
+    n, budget = 32_000_000, 3_500_000_000
+    if resident is not None:
+        monkeypatch.setenv("LEY_EXTERNAL_RESIDENT", resident)
+    hb = ley.ley_host_scratch_bytes(n, mem_budget=budget)
+    if resident is None:
+        assert 0 < hb < n * 100  # some runs stay on the device
+    else:
+        assert hb == n * 100
+    gen = datagen.uniform_records if kind == "uniform" else datagen.skew_records
+    h_in = torch.empty(n, 100, dtype=torch.uint8).pin_memory()
+    for c0 in range(0, n, 8_000_000):
+        c1 = min(n, c0 + 8_000_000)
+        part = gen(c1 - c0, seed=77, device="cuda:0", tag_index=True) if kind == "skew" else \
+            gen(c1 - c0, seed=77, device="cuda:0", start=c0, tag_index=True)
+        if kind == "skew":
+            # the skewed chunks are drawn alike (same seed), so every key
+            # recurs in four runs: ties across runs; the tags are made global
+            part[:, 10:14] = 0
+            idx = torch.arange(c0, c1, dtype=torch.int64, device="cuda:0")
+            for b in range(4):
+                part[:, 10 + b] = ((idx >> (8 * b)) & 0xFF).to(torch.uint8)
+        h_in[c0:c1].copy_(part.cpu())
+    h_out = torch.empty_like(h_in).pin_memory()
+    ley.ley_sort_records(h_in, h_out, key_bytes=10, mem_budget=budget)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    assert orc.check_tagged_threads(h_out.numpy(), h_in.numpy()) == -1
