@@ -885,6 +885,29 @@ class LinkMeter:
              "duplex_each_GBps": nb / timed(lambda: (h2d(), d2h())) / 1e9}
         return {k: round(v, 1) for k, v in r.items()}
 
+    def read_rate(self, host, slice_bytes=1 << 30):
+        """Host->device rate of one given pinned buffer (the sort's own input),
+        read once in `slice_bytes` slices: overall GB/s and the slowest slice.
+        On the shared boxes whole regions of an allocation can read several
+        times slower than the meter's own buffers for seconds at a time."""
+        import torch
+        cu, nb = self.cu, host.nbytes
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        worst, total_ms = None, 0.0
+        for o in range(0, nb, slice_bytes):
+            m = min(slice_bytes, nb - o)
+            ev[0].record(self.s1)
+            assert cu.cuMemcpyHtoDAsync_v2(self.d1.data_ptr(), host.ctypes.data + o, m,
+                                           self.s1.cuda_stream) == 0
+            ev[1].record(self.s1)
+            ev[1].synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            total_ms += ms
+            g = m / (ms * 1e-3) / 1e9
+            worst = g if worst is None else min(worst, g)
+        return {"GBps": round(nb / (total_ms * 1e-3) / 1e9, 1), "slowest_slice_GBps": round(worst, 1),
+                "slice_bytes": slice_bytes}
+
     def close(self):
         host_free(self.h1)
         host_free(self.h2)
@@ -942,9 +965,11 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         for _ in range(warm):
             ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
                                  mem_budget=budget, stream=stream)
-        times, links = [], []
+        times, links, reads = [], [], []
+        h_in_flat = h_in_np.reshape(-1)
         for _ in range(calls):
             links.append(meter.measure())
+            reads.append(meter.read_rate(h_in_flat))
             barrier(pg, dev)
             t0 = time.perf_counter()
             ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
@@ -978,7 +1003,7 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
             meter.close()
     link_b = 2 * n * REC if picked == "partial" else 4 * n * REC
     per_call = []
-    for dt, lk in zip(times, links):
+    for dt, lk, rd in zip(times, links, reads):
         # partial: the copy out waits for the finished order, so the floor is
         # the serial n*100/h2d + n*100/d2h; external: runs in and out, then
         # partitions in and out (2 n*100 bytes each way) with both directions
@@ -990,7 +1015,8 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         floor = serial if picked == "partial" else duplex
         per_call.append({"s": round(dt, 4), "floor_s": round(floor, 4),
                          "frac": round(floor / dt, 4),
-                         "frac_serial_floor": round(serial / dt, 4), "link": lk})
+                         "frac_serial_floor": round(serial / dt, 4), "link": lk,
+                         "input_read": rd})
     med = statistics.median(times)
     fr = [c["frac"] for c in per_call]
     return {

@@ -1012,7 +1012,7 @@ static ley_status stage_merge(const SortArgs& a, const uint8_t* dev_runs, const 
 // after it is already being copied in; runs are about n / kExtRuns records,
 // so that filling and draining this pipeline (the first copy in, the last
 // copy out) costs little next to the copies themselves.
-constexpr ull kExtRuns = 16;
+constexpr ull kExtRuns = 32;
 constexpr int kExtBufs = 3;
 constexpr ull kExtMinRun = 4ull << 20;
 constexpr uint32_t kMaxRuns = 128;  // merge fan-in (the offsets travel in kernel parameters)

@@ -104,12 +104,21 @@ def test_workspace_bytes_under_a_budget(ley):
     assert ley.ley_workspace_bytes(0, mem_budget=budget) == 0
     # pinned host scratch: none in the partial mode; in the external mode the
     # runs that do not stay on the device (a 30 GB budget keeps several of
-    # the 25M-record runs of 6e8 records there)
+    # the 18.75M-record runs of 6e8 records there)
     assert ley.ley_host_scratch_bytes(200_000_000, mem_budget=budget) == 0
     hb = ley.ley_host_scratch_bytes(600_000_000, mem_budget=budget)
     assert 0 < hb < 600_000_000 * 100 and hb % (100 * 4096) == 0
-    # a budget just large enough for the pipeline keeps every run on the host
-    assert ley.ley_host_scratch_bytes(600_000_000, mem_budget=10_000_000_000) == 600_000_000 * 100
+    # a smaller budget keeps fewer runs on the device, never more than it holds
+    hb10 = ley.ley_host_scratch_bytes(600_000_000, mem_budget=10_000_000_000)
+    assert hb < hb10 < 600_000_000 * 100 and hb10 >= 600_000_000 * 100 - 10_000_000_000
+    assert hb >= 600_000_000 * 100 - budget
+    # with no runs kept on the device every run goes to the host
+    import os
+    os.environ["LEY_EXTERNAL_RESIDENT"] = "0"
+    try:
+        assert ley.ley_host_scratch_bytes(600_000_000, mem_budget=budget) == 600_000_000 * 100
+    finally:
+        del os.environ["LEY_EXTERNAL_RESIDENT"]
     with pytest.raises(ley.LeyError) as e:
         ley.ley_host_scratch_bytes(600_000_000, mem_budget=1 << 20)
     assert e.value.status == ley.LEY_ENOMEM
