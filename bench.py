@@ -327,7 +327,11 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
                                        stream=streams[k])
         for st in streams:
             st.synchronize()
-        lp0 = link_peaks(dev)  # the link before the steps (and again after them)
+        meter = LinkMeter(dev)
+        lp0 = meter.measure()  # the link before the steps (and again after them)
+        # the input buffer's own read rate: whole regions of a pinned
+        # allocation can read several times slower than the meter's buffers
+        rd = meter.read_rate(h_in)
         # one blocking call: the latency of a single sort, host to host
         t0 = time.perf_counter()
         ley.ley_sort_records(addr_in, addr_out[0], n=ne, rec_bytes=REC, key_bytes=kb, stream=stream)
@@ -355,14 +359,15 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         # better of the two readings): with both directions busy a step cannot
         # take less than n * REC / duplex_each.  Rates on the shared hosts
         # drift between and within processes.
-        lp1 = link_peaks(dev)
+        lp1 = meter.measure()
+        meter.close()
         lp = {k: max(lp0[k], lp1[k]) for k in lp0}
         floor_ms = ne * REC / (lp["duplex_each_GBps"] * 1e9) * 1e3
         e2e = {"value": round(world * ne * REC / dt / 1e9, 2), "unit": "GB/s",
                "ms_per_step": round(dt * 1e3, 2), "h2d_bytes_per_step": world * ne * REC,
                "d2h_bytes_per_step": world * ne * REC, "streams": ns, "records": ne,
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
-               "link_before": lp0, "link_after": lp1,
+               "link_before": lp0, "link_after": lp1, "input_read": rd,
                "duplex_floor_ms": round(floor_ms, 2),
                "floor_frac": round(floor_ms / (dt * 1e3), 4)}
 
@@ -914,15 +919,6 @@ class LinkMeter:
         del self.d1, self.d2
 
 
-def link_peaks(dev, nbytes=2 << 30, reps=3):
-    """One reading of the link with buffers of its own (see LinkMeter)."""
-    m = LinkMeter(dev, nbytes)
-    try:
-        return m.measure(reps)
-    finally:
-        m.close()
-
-
 def host_avail_bytes():
     try:
         with open("/proc/meminfo") as f:
@@ -1131,7 +1127,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=100_000_000)
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-streams", type=int, default=2,
                     help="streams the end-to-end steps are queued on in turn")
     ap.add_argument("--no-e2e", action="store_true")

@@ -385,9 +385,8 @@ ley_status ley_last_device_status(ley_stream_t stream);
  *   n           at most LEY_NOALLOC_MAX_RECORDS; larger n returns LEY_ENOMEM
  *               before any work.
  * The first call on a device looks up that array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  The call waits for its work on `stream` and returns its device-side
- * status (LEY_ETIMEOUT if a bounded wait gave up).  All calls share the one
+ * device, with that device current).  The call waits for its work on `stream`
+ * and returns its device-side status (LEY_ETIMEOUT if a bounded wait gave up).  All calls share the one
  * array and each leaves its contents behind: calls whose work overlaps on the
  * GPU (other streams, other host threads) race and must be serialised by the
  * caller.

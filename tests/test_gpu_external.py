@@ -84,6 +84,43 @@ def test_queued_partial_sorts_on_two_streams_exact(orc, ley):
         assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy()))
 
 
+def test_queued_partial_sorts_from_several_threads_exact(orc, ley):
+    """Host-memory sorts queued at once from three host threads, each on its
+    own streams, several calls per thread, so that the library's per-call
+    streams, events and pooled scratch are taken from several threads at
+    once; every output equals the oracle's."""
+    import threading
+    jobs = [[] for _ in range(3)]
+    for t in range(3):
+        for i, n in enumerate([4097, 300_001, 77_777]):
+            gen = datagen.skew_records if (t + i) % 2 else datagen.uniform_records
+            rec = gen(n, seed=100 + 10 * t + i).pin_memory()
+            jobs[t].append((rec, torch.zeros_like(rec).pin_memory()))
+    errors = []
+
+    def worker(t):
+        try:
+            torch.cuda.set_device(0)
+            streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+            for i, (rec, out) in enumerate(jobs[t]):
+                ley.ley_sort_records_async(rec, out, key_bytes=10, stream=streams[i % 2])
+            for st in streams:
+                st.synchronize()
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(3)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    for per_thread in jobs:
+        for rec, out in per_thread:
+            assert np.array_equal(out.numpy(), orc.sort_records(rec.numpy()))
+
+
 def test_queued_long_key_sorts_on_two_streams_exact(orc, ley):
     # keys longer than a tuple's 12 bytes (one sort per 12-byte window) in the
     # queued partial mode, two sorts in flight on two streams
