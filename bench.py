@@ -369,7 +369,11 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
                "link_before": lp0, "link_after": lp1, "input_read": rd,
                "duplex_floor_ms": round(floor_ms, 2),
-               "floor_frac": round(floor_ms / (dt * 1e3), 4)}
+               "floor_frac": round(floor_ms / (dt * 1e3), 4),
+               # every step copies its input in: at the rate the input buffer
+               # itself read at just before the steps, if that is the lower
+               "input_floor_frac": round(
+                   ne * REC / (min(lp["duplex_each_GBps"], rd["GBps"]) * 1e9) / dt, 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -1009,12 +1013,24 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
             serial *= 2
         duplex = 2 * n * REC / (lk["duplex_each_GBps"] * 1e9)
         floor = serial if picked == "partial" else duplex
+        # Either mode writes no output before it has read all of its input
+        # (the sorted order needs every key; the merge needs every run): the
+        # input read at the rate its own buffer gave just before the call,
+        # then the output written at the D2H rate, estimates the floor on
+        # this buffer whatever the link meter's buffers read.  An estimate
+        # only: the buffer's rate drifts during the call, so the fraction can
+        # come out above 1.
+        in_rate = min(lk["h2d_GBps"], rd["GBps"])
+        floor_in = n * REC / (in_rate * 1e9) + n * REC / (lk["d2h_GBps"] * 1e9)
         per_call.append({"s": round(dt, 4), "floor_s": round(floor, 4),
                          "frac": round(floor / dt, 4),
-                         "frac_serial_floor": round(serial / dt, 4), "link": lk,
+                         "frac_serial_floor": round(serial / dt, 4),
+                         "input_floor_s": round(floor_in, 4),
+                         "frac_input_floor": round(floor_in / dt, 4), "link": lk,
                          "input_read": rd})
     med = statistics.median(times)
     fr = [c["frac"] for c in per_call]
+    fi = [c["frac_input_floor"] for c in per_call]
     return {
         "mode": picked, "records": n, "bytes": n * REC, "budget_bytes": budget,
         "device_bytes": ws, "calls": calls, "warmup": warm,
@@ -1022,6 +1038,7 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         "GBps": round(world * n * REC / med / 1e9, 2),
         "link_GBps": round(link_b / med / 1e9, 2),
         "frac_median": round(statistics.median(fr), 4), "frac_min": min(fr), "frac_max": max(fr),
+        "frac_input_floor_median": round(statistics.median(fi), 4),
         "floor": ("serial: n*100/h2d + n*100/d2h" if picked == "partial"
                   else "duplex: 2*n*100 / (rate each way with both directions busy)"),
         "per_call": per_call, "link_after": link_after, "parity": parity,
