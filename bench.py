@@ -332,6 +332,7 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
         # the input buffer's own read rate: whole regions of a pinned
         # allocation can read several times slower than the meter's buffers
         rd = meter.read_rate(h_in)
+        wr = meter.write_rate(h_outs[0])  # overwritten by the steps
         # one blocking call: the latency of a single sort, host to host
         t0 = time.perf_counter()
         ley.ley_sort_records(addr_in, addr_out[0], n=ne, rec_bytes=REC, key_bytes=kb, stream=stream)
@@ -368,12 +369,15 @@ def _run_workload(args, world, rank, local, pg, dev, stream, wl, n):
                "d2h_bytes_per_step": world * ne * REC, "streams": ns, "records": ne,
                "single_call_ms": round(lat * 1e3, 2), "link": lp,
                "link_before": lp0, "link_after": lp1, "input_read": rd,
+               "output_write": wr,
                "duplex_floor_ms": round(floor_ms, 2),
                "floor_frac": round(floor_ms / (dt * 1e3), 4),
-               # every step copies its input in: at the rate the input buffer
-               # itself read at just before the steps, if that is the lower
-               "input_floor_frac": round(
-                   ne * REC / (min(lp["duplex_each_GBps"], rd["GBps"]) * 1e9) / dt, 4)}
+               # every step copies its input in and its output out: at the
+               # rates these buffers themselves gave just before the steps,
+               # where those are the lower
+               "buffer_floor_frac": round(
+                   ne * REC / (min(lp["duplex_each_GBps"], rd["GBps"], wr["GBps"]) * 1e9) / dt,
+                   4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -899,6 +903,14 @@ class LinkMeter:
         read once in `slice_bytes` slices: overall GB/s and the slowest slice.
         On the shared boxes whole regions of an allocation can read several
         times slower than the meter's own buffers for seconds at a time."""
+        return self._buffer_rate(host, slice_bytes, True)
+
+    def write_rate(self, host, slice_bytes=1 << 30):
+        """Device->host rate into one given pinned buffer (the sort's own
+        output, overwritten), in `slice_bytes` slices, as read_rate."""
+        return self._buffer_rate(host, slice_bytes, False)
+
+    def _buffer_rate(self, host, slice_bytes, to_device):
         import torch
         cu, nb = self.cu, host.nbytes
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -906,8 +918,12 @@ class LinkMeter:
         for o in range(0, nb, slice_bytes):
             m = min(slice_bytes, nb - o)
             ev[0].record(self.s1)
-            assert cu.cuMemcpyHtoDAsync_v2(self.d1.data_ptr(), host.ctypes.data + o, m,
-                                           self.s1.cuda_stream) == 0
+            if to_device:
+                assert cu.cuMemcpyHtoDAsync_v2(self.d1.data_ptr(), host.ctypes.data + o, m,
+                                               self.s1.cuda_stream) == 0
+            else:
+                assert cu.cuMemcpyDtoHAsync_v2(host.ctypes.data + o, self.d2.data_ptr(), m,
+                                               self.s1.cuda_stream) == 0
             ev[1].record(self.s1)
             ev[1].synchronize()
             ms = ev[0].elapsed_time(ev[1])
@@ -965,11 +981,12 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         for _ in range(warm):
             ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
                                  mem_budget=budget, stream=stream)
-        times, links, reads = [], [], []
-        h_in_flat = h_in_np.reshape(-1)
+        times, links, reads, writes = [], [], [], []
+        h_in_flat, h_out_flat = h_in_np.reshape(-1), h_out_np.reshape(-1)
         for _ in range(calls):
             links.append(meter.measure())
             reads.append(meter.read_rate(h_in_flat))
+            writes.append(meter.write_rate(h_out_flat))  # the call overwrites it
             barrier(pg, dev)
             t0 = time.perf_counter()
             ley.ley_sort_records(h_in, h_out, n=n, rec_bytes=REC, key_bytes=KEY,
@@ -1003,7 +1020,7 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
             meter.close()
     link_b = 2 * n * REC if picked == "partial" else 4 * n * REC
     per_call = []
-    for dt, lk, rd in zip(times, links, reads):
+    for dt, lk, rd, wr in zip(times, links, reads, writes):
         # partial: the copy out waits for the finished order, so the floor is
         # the serial n*100/h2d + n*100/d2h; external: runs in and out, then
         # partitions in and out (2 n*100 bytes each way) with both directions
@@ -1016,21 +1033,22 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         # Either mode writes no output before it has read all of its input
         # (the sorted order needs every key; the merge needs every run): the
         # input read at the rate its own buffer gave just before the call,
-        # then the output written at the D2H rate, estimates the floor on
-        # this buffer whatever the link meter's buffers read.  An estimate
-        # only: the buffer's rate drifts during the call, so the fraction can
-        # come out above 1.
+        # then the output written at the rate its own buffer took, estimates
+        # the floor on these buffers whatever the link meter's buffers read.
+        # An estimate only: a buffer's rate drifts during the call, so the
+        # fraction can come out above 1.
         in_rate = min(lk["h2d_GBps"], rd["GBps"])
-        floor_in = n * REC / (in_rate * 1e9) + n * REC / (lk["d2h_GBps"] * 1e9)
+        out_rate = min(lk["d2h_GBps"], wr["GBps"])
+        floor_buf = n * REC / (in_rate * 1e9) + n * REC / (out_rate * 1e9)
         per_call.append({"s": round(dt, 4), "floor_s": round(floor, 4),
                          "frac": round(floor / dt, 4),
                          "frac_serial_floor": round(serial / dt, 4),
-                         "input_floor_s": round(floor_in, 4),
-                         "frac_input_floor": round(floor_in / dt, 4), "link": lk,
-                         "input_read": rd})
+                         "buffer_floor_s": round(floor_buf, 4),
+                         "frac_buffer_floor": round(floor_buf / dt, 4), "link": lk,
+                         "input_read": rd, "output_write": wr})
     med = statistics.median(times)
     fr = [c["frac"] for c in per_call]
-    fi = [c["frac_input_floor"] for c in per_call]
+    fi = [c["frac_buffer_floor"] for c in per_call]
     return {
         "mode": picked, "records": n, "bytes": n * REC, "budget_bytes": budget,
         "device_bytes": ws, "calls": calls, "warmup": warm,
@@ -1038,7 +1056,7 @@ def host_mode_run(args, dev, stream, pg, world, mode, n, budget, calls, warm, me
         "GBps": round(world * n * REC / med / 1e9, 2),
         "link_GBps": round(link_b / med / 1e9, 2),
         "frac_median": round(statistics.median(fr), 4), "frac_min": min(fr), "frac_max": max(fr),
-        "frac_input_floor_median": round(statistics.median(fi), 4),
+        "frac_buffer_floor_median": round(statistics.median(fi), 4),
         "floor": ("serial: n*100/h2d + n*100/d2h" if picked == "partial"
                   else "duplex: 2*n*100 / (rate each way with both directions busy)"),
         "per_call": per_call, "link_after": link_after, "parity": parity,

@@ -1268,19 +1268,19 @@ struct FinShared {
 
 // Rank of tuple tv among the c tuples at B[s..s+c) (strict (key, index) order).
 // The order of tup_less, evaluated without branches: every tuple of the
-// sub-bucket is compared, so the lanes of a warp stay together.
+// sub-bucket is compared, so the lanes of a warp stay together.  The key
+// bits of z and the index w compare as one 64-bit word (z's bits above w's).
 __device__ __forceinline__ uint32_t cmp_rank(const uint4* B, uint32_t s, uint32_t c,
                                              const uint4& tv, uint32_t lo_mask) {
     const ull kv = key_hi(tv);
-    const uint32_t lv = tv.z & lo_mask;
+    const ull lv = ((ull)(tv.z & lo_mask) << 32) | tv.w;
     uint32_t r = 0;
 #pragma unroll 4
     for (uint32_t j = 0; j < c; j++) {
         const uint4 u = B[s + j];
         const ull ku = key_hi(u);
-        const uint32_t lu = u.z & lo_mask;
-        const bool lt_lo = lu < lv || (lu == lv && u.w < tv.w);
-        r += (ku < kv || (ku == kv && lt_lo)) ? 1u : 0u;
+        const ull lu = ((ull)(u.z & lo_mask) << 32) | u.w;
+        r += (ku < kv || (ku == kv && lu < lv)) ? 1u : 0u;
     }
     return r;
 }
