@@ -1268,19 +1268,28 @@ struct FinShared {
 
 // Rank of tuple tv among the c tuples at B[s..s+c) (strict (key, index) order).
 // The order of tup_less, evaluated without branches: every tuple of the
-// sub-bucket is compared, so the lanes of a warp stay together.  The key
-// bits of z and the index w compare as one 64-bit word (z's bits above w's).
+// sub-bucket is compared, so the lanes of a warp stay together.  The whole
+// order is one 128-bit unsigned comparison (key bytes 0-7, the key bits of z,
+// then the index w, most significant first), taken as the borrow out of a
+// four-word subtraction chain.
 __device__ __forceinline__ uint32_t cmp_rank(const uint4* B, uint32_t s, uint32_t c,
                                              const uint4& tv, uint32_t lo_mask) {
-    const ull kv = key_hi(tv);
-    const ull lv = ((ull)(tv.z & lo_mask) << 32) | tv.w;
+    const uint32_t vz = tv.z & lo_mask;
     uint32_t r = 0;
 #pragma unroll 4
     for (uint32_t j = 0; j < c; j++) {
         const uint4 u = B[s + j];
-        const ull ku = key_hi(u);
-        const ull lu = ((ull)(u.z & lo_mask) << 32) | u.w;
-        r += (ku < kv || (ku == kv && lu < lv)) ? 1u : 0u;
+        uint32_t t, m;
+        // borrow out of u - tv over the words (w, z & mask, x, y), least significant first
+        asm("sub.cc.u32 %0, %2, %6;\n\t"
+            "subc.cc.u32 %0, %3, %7;\n\t"
+            "subc.cc.u32 %0, %4, %8;\n\t"
+            "subc.cc.u32 %0, %5, %9;\n\t"
+            "subc.u32 %1, %10, %10;"
+            : "=&r"(t), "=r"(m)
+            : "r"(u.w), "r"(u.z & lo_mask), "r"(u.x), "r"(u.y), "r"(tv.w), "r"(vz), "r"(tv.x),
+              "r"(tv.y), "r"(0u));
+        r -= m;  // m = 0xFFFFFFFF when u < tv
     }
     return r;
 }
