@@ -184,10 +184,19 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t* cnt, uint32_t dg, bool v
 // digit -- distinct digits of the warp's own row -- stores the count advanced
 // by its peers.  Faster where few warps rank at once (the finishing CTAs);
 // the atomic form is faster in the scatter pass.
+// MATCH: the peers from one match instruction instead of the eight ballots
+// (measured on the finishing kernel: faster for records, chiefly on skewed
+// keys, slower for the 8-byte keys of pairs).
+template <bool MATCH>
 __device__ __forceinline__ uint32_t warp_rank_rw(uint32_t* cnt, uint32_t dg, bool valid,
                                                  uint32_t lt_mask) {
-    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-    const uint32_t peers = peers8(dg) & vmask;
+    uint32_t peers;
+    if constexpr (MATCH) {
+        peers = __match_any_sync(0xffffffffu, valid ? dg : 256u + (threadIdx.x & 31u));
+    } else {
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        peers = peers8(dg) & vmask;
+    }
     const uint32_t old = valid ? cnt[dg] : 0u;
     __syncwarp();
     if (valid && (peers & lt_mask) == 0) cnt[dg] = old + (uint32_t)__popc(peers);
@@ -1328,7 +1337,7 @@ __device__ __forceinline__ void stack_push(FinShared& S, uint32_t s, uint32_t c,
 // key-difference mask reduced to find the first digit where keys differ.
 // Sub-buckets are finished here by comparison ranking when tiny, else
 // queued for a warp (<= kWarpMax) or pushed for the whole CTA.
-template <bool FROM_GLOBAL>
+template <bool FROM_GLOBAL, bool MATCH>
 __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0,
                                uint32_t c, int d0, const KeySpec& ks, uint32_t* err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1361,7 +1370,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             if ((uint32_t)k >= ipt || wbase + k * 32 >= c) continue;  // no item of the warp: skip
             const bool valid = idx < c;
             const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
-            rd[k] = (warp_rank_rw(S.cnt[warp], dk, valid, lt_mask) << 8) | dk;
+            rd[k] = (warp_rank_rw<MATCH>(S.cnt[warp], dk, valid, lt_mask) << 8) | dk;
         }
         __syncthreads();
         {
@@ -1452,6 +1461,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
 // One warp sorts the c <= kWarpMax tuples at B[s, s+c) from digit d0 on:
 // a stable counting pass on the first digit where they differ, comparison
 // ranking of tiny sub-buckets, and larger ones back onto the queue.
+template <bool MATCH>
 __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, int d0,
                               const KeySpec& ks, uint32_t* err) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1491,7 +1501,7 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
         if (k * 32 >= (int)c) continue;  // no item of the warp: skip
         const bool valid = idx < c;
         const uint32_t dk = valid ? digit_of(v[k], ds) : 0u;
-        rd[k] = (warp_rank_rw(cnt, dk, valid, lt_mask) << 8) | dk;
+        rd[k] = (warp_rank_rw<MATCH>(cnt, dk, valid, lt_mask) << 8) | dk;
     }
     __syncwarp();
     // Exclusive scan of the 256 counters: lane l owns bins 8l..8l+7.
@@ -1544,6 +1554,7 @@ __device__ void fin_warp_sort(uint4* B, FinShared& S, uint32_t s, uint32_t c, in
 
 // Warps take queued sub-buckets until every queued one is finished
 // (the small-bucket queue of Algorithm 1, drained by the CTA's warps).
+template <bool MATCH>
 __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint32_t* err) {
     const int lane = threadIdx.x & 31;
     uint32_t idle = 0;
@@ -1579,7 +1590,7 @@ __device__ void fin_drain_queue(uint4* B, FinShared& S, const KeySpec& ks, uint3
             ok = __shfl_sync(0xffffffffu, ok, 0);
             const uint32_t s0 = meta & 0xFFFFu, c0 = meta >> 16;
             if (ok && s0 + c0 <= (uint32_t)kSmall && c0 <= (uint32_t)kWarpMax)
-                fin_warp_sort(B, S, s0, c0, (int)dg, ks, err);
+                fin_warp_sort<MATCH>(B, S, s0, c0, (int)dg, ks, err);
             else if (lane == 0)
                 LEY_FAIL(err, kErrCapacity);
             __syncwarp();
@@ -1708,6 +1719,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
     const ull nfin = w.ctl->fin_count < w.cap_fin ? w.ctl->fin_count : w.cap_fin;
     const int tid = threadIdx.x;
     constexpr int TM = TaskEmit<MODE>::mode;  // how a task is emitted
+    constexpr bool kMatch = TM != 1;          // records: match ranks; pairs: ballots
     for (int i = tid; i < kFinQueue; i += kFinThreads) S.q_ready[i] = 0;
     if (tid == 0) S.task = atomicAdd(&w.ctl->fin_ctr, 1u);
     while (true) {
@@ -1740,10 +1752,10 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             skip = true;
         }
         if (!skip) {
-            fin_block_pass<true>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
+            fin_block_pass<true, kMatch>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
             __syncthreads();
             while (S.q_tail != 0 || S.bs_n != 0) {
-                fin_drain_queue(B, S, ks, w.err);
+                fin_drain_queue<kMatch>(B, S, ks, w.err);
                 __syncthreads();
                 const int ns = S.bs_n;
                 if (ns <= 0) break;
@@ -1760,7 +1772,7 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
                     __syncthreads();
                     continue;
                 }
-                fin_block_pass<false>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
+                fin_block_pass<false, kMatch>(B, S, src, meta & 0xFFFFu, meta >> 16, dg, ks, w.err);
                 __syncthreads();
             }
             if constexpr (TM == 2) {
