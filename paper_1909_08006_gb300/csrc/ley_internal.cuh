@@ -26,8 +26,8 @@ constexpr int kPassTile = 4096;
 constexpr int kPassThreads = 512;
 constexpr int kPassItems = kPassTile / kPassThreads;   // 8
 constexpr int kPassWarps = kPassThreads / 32;          // 16
-constexpr int kHistThreads = 256;
-constexpr int kHistItems = kPassTile / kHistThreads;   // 16
+constexpr int kHistThreads = 512;
+constexpr int kHistItems = kPassTile / kHistThreads;   // 8
 // Tiles per chunk of the per-tile offset scan.
 constexpr int kScanChunk = 16;
 constexpr uint32_t kNoPass = 0xFFFFFFFFu;

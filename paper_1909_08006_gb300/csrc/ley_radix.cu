@@ -590,7 +590,7 @@ k_hist(Work w, KeySpec ks, int L) {
     }
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        sh_hist[tid] = 0;
+        if (tid < kRadix) sh_hist[tid] = 0;
         if (tid < 3) sh_d[tid] = 0;
         // Thread 0 asks the L2 for this CTA's next tile (looked up in steps,
         // so that no load is waited for at once).
@@ -639,7 +639,7 @@ k_hist(Work w, KeySpec ks, int L) {
             }
         }
         __syncthreads();
-        w.tile_cnt[(ull)t * kRadix + tid] = sh_hist[tid];
+        if (tid < kRadix) w.tile_cnt[(ull)t * kRadix + tid] = sh_hist[tid];
         if (tid == 0) flush_diff(sh_d, &w.diff[p][s]);
     }
 }
