@@ -365,7 +365,7 @@ static ley_status stage_levels(const Work& w, const KeySpec& ks, cudaStream_t st
     const LaunchCfg cp{pass_grid(sms, t), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
-    const LaunchCfg cc{2 * sms, 128, 0, st};
+    const LaunchCfg cc{8 * sms, 128, 0, st};
     for (int lvl = 0; lvl < ks.ndig; lvl++) {
         if (lvl > 0) LEY_TRY(launch("hist", st, [&] { return launch_hist(ch, w, ks, lvl); }));
         LEY_TRY(launch("scan", st, [&] { return launch_scan(cs, w, lvl); }));
@@ -2106,7 +2106,7 @@ static ley_status enqueue_records_noalloc(const SortArgs& a, char* base, const L
     const LaunchCfg cp{sms * blocks_per_sm(KK_PASS), kPassThreads, kernel_smem(KK_PASS), st};
     const LaunchCfg cs{sms * blocks_per_sm(KK_SCAN), kRadix, 0, st};
     const LaunchCfg ch{sms * blocks_per_sm(KK_HIST), kHistThreads, 0, st};
-    const LaunchCfg cc{2 * sms, 128, 0, st};
+    const LaunchCfg cc{8 * sms, 128, 0, st};
     for (int lvl = 0; lvl < ks.ndig; lvl++) {
         if (lvl > 0) LEY_TRY(launch_hist(ch, w, ks, lvl));
         LEY_TRY(launch_scan(cs, w, lvl));
