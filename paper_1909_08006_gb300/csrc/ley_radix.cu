@@ -994,7 +994,7 @@ k_classify(Work w, KeySpec ks, int L) {
             f.count = gc >> 1;
             f.digit = (uint16_t)((gc & 1u) ? d1 : sg.digit);
             f.buf = (uint8_t)nb;
-            f.flags = 0;
+            f.flags = (gc & 1u) ? 0 : 2;  // 2: sub-buckets of one bucket, in `digit` order
             w.fin[base + i] = f;
         }
         __syncwarp();
@@ -1339,7 +1339,8 @@ __device__ __forceinline__ void stack_push(FinShared& S, uint32_t s, uint32_t c,
 // queued for a warp (<= kWarpMax) or pushed for the whole CTA.
 template <bool FROM_GLOBAL, bool MATCH>
 __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32_t r0,
-                               uint32_t c, int d0, const KeySpec& ks, uint32_t* err) {
+                               uint32_t c, int d0, const KeySpec& ks, uint32_t* err,
+                               bool grouped = false) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = lanemask_lt();
     // Items per thread for this range, so that every warp holds a share:
@@ -1359,6 +1360,32 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             v[k] = idx < c ? B[r0 + idx] : ref;
     }
     int ds = d0 < ks.ndig ? d0 : ks.ndig - 1;
+    if (FROM_GLOBAL && grouped) {
+        // A packed task: whole sub-buckets of one bucket, already in the order
+        // of digit ds, so a counting pass would leave every tuple in place.
+        // The tuples are staged where they are and each sub-bucket's bounds
+        // are found where the digit changes (sb_cnt holds the end until the
+        // last step).
+        S.sb_cnt[tid] = 0;  // one digit per thread
+#pragma unroll
+        for (int k = 0; k < kFinItems; k++) {
+            const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
+            if (idx < c) B[r0 + idx] = v[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kFinItems; k++) {
+            const uint32_t idx = (uint32_t)k < ipt ? wbase + k * 32 + lane : c;
+            if (idx < c) {
+                const uint32_t dk = digit_of(v[k], ds);
+                if (idx == 0 || digit_of(B[r0 + idx - 1], ds) != dk) S.sb_off[dk] = (uint16_t)idx;
+                if (idx + 1 == c || digit_of(B[r0 + idx + 1], ds) != dk)
+                    S.sb_cnt[dk] = (uint16_t)(idx + 1);
+            }
+        }
+        __syncthreads();
+        if (S.sb_cnt[tid]) S.sb_cnt[tid] = (uint16_t)(S.sb_cnt[tid] - S.sb_off[tid]);
+    } else {
     for (;;) {
 #pragma unroll
         for (int ww = 0; ww < kFinWarps; ww++) S.cnt[ww][tid] = 0;
@@ -1436,6 +1463,7 @@ __device__ void fin_block_pass(uint4* B, FinShared& S, const uint4* gsrc, uint32
             if (pos < r0 + c) B[pos] = v[k];
             else LEY_FAIL(err, kErrCapacity);  // inconsistent ranks: never
         }
+    }
     }
     __syncthreads();
     {
@@ -1752,7 +1780,8 @@ k_finish(Work w, KeySpec ks, Emitter<MODE> emit) {
             skip = true;
         }
         if (!skip) {
-            fin_block_pass<true, kMatch>(B, S, src, 0, tk.count, tk.digit, ks, w.err);
+            fin_block_pass<true, kMatch>(B, S, src, 0, tk.count, tk.digit, ks, w.err,
+                                         (tk.flags & 2) != 0);
             __syncthreads();
             while (S.q_tail != 0 || S.bs_n != 0) {
                 fin_drain_queue<kMatch>(B, S, ks, w.err);
