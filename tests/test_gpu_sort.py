@@ -215,7 +215,7 @@ def test_error_codes(ley):
 
 # ------------------------------------------------------ full-size runs
 
-def _full(ley, orc, rec_gen, n):
+def _full(ley, orc, rec_gen, n, samples=16, threads=False):
     """Sort n tagged records on the GPU; verify with the O(n) complete check
     (permutation, byte equality with the input, strict (key, index) order)."""
     d_in = rec_gen(n)
@@ -227,10 +227,11 @@ def _full(ley, orc, rec_gen, n):
     host_out = d_out.cpu().numpy()
     del d_out
     torch.cuda.empty_cache()
-    assert orc.check_tagged(host_out, host_in) == -1
+    check = orc.check_tagged_threads if threads else orc.check_tagged
+    assert check(host_out, host_in) == -1
     # sampled positions from the definition: rank(i) scans all n records
     rng = np.random.default_rng(1)
-    samples = np.sort(rng.choice(n, 16, replace=False)).astype(np.uint64)
+    samples = np.sort(rng.choice(n, samples, replace=False)).astype(np.uint64)
     ranks = orc.rank_records(host_in, samples)
     for i, r in zip(samples, ranks):
         assert np.array_equal(host_out[int(r)], host_in[int(i)])
@@ -244,6 +245,15 @@ def test_full_size_uniform_1e8(orc, ley):
 def test_full_size_skew_1e8(orc, ley):
     n = 100_000_000
     _full(ley, orc, lambda m: datagen.skew_records(m, seed=3, device=DEV, tag_index=True), n)
+
+
+def test_full_size_uniform_4e8(orc, ley):
+    # four times the 10 GB workload in one internal sort (40 GB in and out of
+    # HBM, record indices up to 4e8): the largest size whose complete check
+    # fits the host's memory beside the two copies
+    n = 400_000_000
+    _full(ley, orc, lambda m: datagen.uniform_records(m, seed=4, device=DEV, tag_index=True), n,
+          samples=4, threads=True)
 
 
 def test_generator_same_on_gpu_and_cpu():
