@@ -256,6 +256,25 @@ def test_full_size_uniform_4e8(orc, ley):
           samples=4, threads=True)
 
 
+@pytest.mark.parametrize("distinct", [0, 1000])
+def test_full_size_pairs_1e8(orc, ley, distinct):
+    # 1e8 (u64 key, u32 index) pairs, uniform keys or keys from 1000 values
+    # (runs of ~1e5 equal keys); the payload is the input position, so the
+    # O(n) check verifies the permutation, the keys and the strict
+    # (key, index) order of the whole output
+    n = 100_000_000
+    if distinct:
+        keys, idx = datagen.narrow_pairs(n, seed=7, distinct=distinct, device=DEV)
+    else:
+        keys, idx = datagen.uniform_pairs(n, seed=6, device=DEV)
+    ko, io = torch.empty_like(keys), torch.empty_like(idx)
+    ley.ley_sort_keys_index(keys, idx, ko, io)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    k_in = keys.cpu().numpy().view(np.uint64)
+    bad = orc.check_pairs_tagged(ko.cpu().numpy(), io.cpu().numpy(), k_in)
+    assert bad == -1, bad
+
+
 def test_generator_same_on_gpu_and_cpu():
     a = datagen.uniform_records(5000, seed=9, device=DEV).cpu()
     b = datagen.uniform_records(5000, seed=9)
