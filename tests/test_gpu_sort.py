@@ -256,6 +256,20 @@ def test_full_size_uniform_4e8(orc, ley):
           samples=4, threads=True)
 
 
+@pytest.mark.parametrize("kind", ["few_distinct", "prefix_shared", "two_symbol"])
+def test_full_size_degenerate_1e8(orc, ley, kind):
+    # degenerate keys at the full 10 GB size: equal runs of ~2e7 records cut
+    # into finishing pieces, keys that differ only in their last two bytes,
+    # keys from a two-letter alphabet (ties on every digit)
+    def gen(m):
+        rec = datagen.edge_records(kind, m, seed=11, device=DEV)
+        i = torch.arange(m, dtype=torch.int64, device=DEV)
+        for b in range(4):  # input positions at bytes 10..13, little-endian
+            rec[:, 10 + b] = ((i >> (8 * b)) & 0xFF).to(torch.uint8)
+        return rec
+    _full(ley, orc, gen, 100_000_000, samples=4, threads=True)
+
+
 @pytest.mark.parametrize("distinct", [0, 1000])
 def test_full_size_pairs_1e8(orc, ley, distinct):
     # 1e8 (u64 key, u32 index) pairs, uniform keys or keys from 1000 values
