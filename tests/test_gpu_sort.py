@@ -270,6 +270,21 @@ def test_full_size_degenerate_1e8(orc, ley, kind):
     _full(ley, orc, gen, 100_000_000, samples=4, threads=True)
 
 
+@pytest.mark.parametrize("rec_bytes,key_bytes", [(104, 12), (16, 8)])
+def test_large_other_geometries(orc, ley, rec_bytes, key_bytes):
+    # 3e7 records of other sizes (permutation plus the generic gather), the
+    # input position tagged right after the key
+    n = 30_000_000
+    d_in = datagen.uniform_records(n, seed=rec_bytes, rec_bytes=rec_bytes, device=DEV,
+                                   tag_index=True, tag_offset=key_bytes)
+    d_out = torch.empty_like(d_in)
+    ley.ley_sort_records(d_in, d_out, key_bytes=key_bytes)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    bad = orc.check_tagged_threads(d_out.cpu().numpy(), d_in.cpu().numpy(), key_bytes=key_bytes,
+                                   tag_offset=key_bytes)
+    assert bad == -1, bad
+
+
 @pytest.mark.parametrize("distinct", [0, 1000])
 def test_full_size_pairs_1e8(orc, ley, distinct):
     # 1e8 (u64 key, u32 index) pairs, uniform keys or keys from 1000 values
