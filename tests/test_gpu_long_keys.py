@@ -88,3 +88,23 @@ def test_long_keys_unsupported_paths(ley):
     with pytest.raises(ley.LeyError) as e:
         ley.ley_sort_records_batch([(d, torch.empty_like(d))], key_bytes=20)
     assert e.value.status == ley.LEY_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("key_bytes", [20, 30])
+def test_long_keys_at_2e7(orc, ley, key_bytes):
+    # 2e7 ASCII records (2 GB) with a shared 9-byte prefix and a 4-letter
+    # alphabet: two and three 12-byte windows over many ties; the input
+    # position is written right after the key and the complete O(n) check
+    # verifies permutation, bytes and strict (key, position) order
+    n = 20_000_000
+    rec = datagen.ascii_records(n, seed=key_bytes, key_bytes=key_bytes, shared_prefix=9,
+                                alphabet=4, device=DEV)
+    i = torch.arange(n, dtype=torch.int64, device=DEV)
+    for b in range(4):
+        rec[:, key_bytes + b] = ((i >> (8 * b)) & 0xFF).to(torch.uint8)
+    out = torch.empty_like(rec)
+    ley.ley_sort_records(rec, out, key_bytes=key_bytes)
+    assert ley.ley_last_device_status() == ley.LEY_OK
+    bad = orc.check_tagged_threads(out.cpu().numpy(), rec.cpu().numpy(), key_bytes=key_bytes,
+                                   tag_offset=key_bytes)
+    assert bad == -1, bad
